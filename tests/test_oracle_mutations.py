@@ -1,0 +1,54 @@
+"""Each pin set must catch a plausible mistake planted in the oracle.
+
+A copy of oracle.c is edited in a temporary directory (one mistake per copy:
+a dropped term, a wrong sign, a transposed operand, a wrong index), compiled,
+and the pin checks of test_oracle_pins.py are run against it.  At least one
+check must fail for every mutant.  The real oracle is never modified.
+"""
+
+import os
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+MUTATIONS = {
+    "drop_d_ratio": ("return zb * zb * (1.0 + c->d_ratio * zb);", "return zb * zb;"),
+    "alpha_sign": ("const double xc = (z3 + alpha) / z1 * x1;", "const double xc = (z3 - alpha) / z1 * x1;"),
+    "k_transposed": ("double k = z1 / (z3 - z1);\n    return c->alpha0",
+                     "double k = (z3 - z1) / z1;\n    return c->alpha0"),
+    "dx3_wrong_layer": ("double z1 = c->z[c->iter_layers[it][0]], z3 = c->z[c->iter_layers[it][2]];\n    return c->dx3_scale",
+                        "double z1 = c->z[c->iter_layers[it][0]], z3 = c->z[c->iter_layers[it][1]];\n    return c->dx3_scale"),
+    "fit_unscale": ("for (int j = 0; j < 3; ++j) th[j] = y[j] * sc[j];",
+                    "for (int j = 0; j < 3; ++j) th[j] = y[j] / sc[j];"),
+    "chi2_sigma": ("fit_xz(c, nx, fz, fx, th) / (c->sigma_x * c->sigma_x)", "fit_xz(c, nx, fz, fx, th) / c->sigma_x"),
+    "ext_tol_half": ("hits[xslot_of_layer(L)] = closest_hit(E, 2 * L + half, xp, c->ext_tol, sc,",
+                     "hits[xslot_of_layer(L)] = closest_hit(E, 2 * L + half, xp, 0.5 * c->ext_tol, sc,"),
+    "clone_rule": ("cd->keep = owned >= 3 || (owned >= 2 && cd->nx == 6);", "cd->keep = owned >= 2;"),
+    "uv_y_sign": ("const double y = (XI - xh) / tI;", "const double y = (xh - XI) / tI;"),
+    "match_dropped_E": (" + c->zmx[4] * txV * txV;", ";"),
+    "match_wrong_z": ("(xS + (zmx - c->z_state) * txS)", "(xS + (zmx - c->z_velo) * txS)"),
+    "toly_no_ty": ("const double rho = txV * txV + tyV * tyV;", "const double rho = txV * txV;"),
+    "state_slope": ("s->tx_s = cd->th[1] + cd->th[2] * (2.0 * zb + 3.0 * c->d_ratio * zb * zb);",
+                    "s->tx_s = cd->th[1];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path, zmx_calibrated):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) == 1, f"mutation site not unique: {name}"
+    mpath = tmp_path / "oracle_mut.c"
+    mpath.write_text(src.replace(old, new))
+    so = oracle.build(force=True, src=str(mpath), out=str(tmp_path / "liboracle_mut.so"))
+    L = oracle.lib(so)
+    failed = []
+    for chk in pins.ALL_CHECKS:
+        kw = {"zmx": zmx_calibrated} if chk is pins.check_noise_free_recovery else {}
+        try:
+            chk(L, **kw)
+        except AssertionError:
+            failed.append(chk.__name__)
+    assert failed, f"no pin caught mutation {name}"
