@@ -1,0 +1,474 @@
+#!/usr/bin/env python3
+"""Benchmark: events/s of SciFi Seeding + VELO-SciFi Matching on GB300.
+
+Workload: the Run-3-like batch (1000 events, Poisson(150) tracks per event,
+30% noise, ~2300 hits/event, VELO = truth + 20% ghosts), synthetic and seeded.
+One step = seeding + matching over the whole batch with the inputs resident in
+HBM, replayed as one CUDA graph of persistent work-queue kernels.  The L2 is
+flushed (256 MB write) between timed steps, outside the timed interval.
+
+Reported beside the batched number (one JSON line on stdout):
+  e2e           the same batch through pipeline_submit / pipeline_poll with
+                host buffers (copies in the timed region), one batch at a time
+  per_event     the plain per-event launch: seeding_run + matching_run per
+                event on one stream
+  served        continuous batching of a Poisson request stream (batch sizes
+                log-uniform 1-4096, log-normal occupancy): events/s, p50/p99
+  roofline      the seeding kernel's FP32 work (units counted by the kernels,
+                per-unit costs fixed in the design doc) per CUDA-event-timed launch
+                against the FP32 peak; its HBM traffic from the ncu summary
+  cpu_baseline  the FP64 oracle on the host cores, bounded sample
+
+`--impl reference` times the oracle (the reference implementation of this
+build) on the same workload instead.  Under torchrun each rank runs its own
+replica batch; the max step time over ranks is used (no data exchange).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "run3"
+METRIC = "events/s (Seeding+Matching) on 1 GB300, batched/served vs per-event launch; p99 latency"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+N_SMS = 152
+FP32_LANES_PER_SM = 128
+
+# Per-unit FP32 operation costs of the seeding and matching steps (the
+# algorithmic work model; units are counted by the kernels themselves).
+OPS_PER_UNIT = {"pairs": 12.0, "triplets": 40.0, "fits": 120.0, "uv_init": 60.0, "match_pairs": 45.0}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(np.max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("st_kernels.cu", "st_device.cuh", "st_kernels.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2606_14480_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(kernel)
+        if e and e.get("source_hash") == kernel_source_hash() and e.get("workload") == WORKLOAD:
+            return float(e["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) timing
+# ---------------------------------------------------------------------------
+
+def time_oracle(batch, zmx, budget_s=12.0, events=None):
+    """Seeding + matching of events by the FP64 oracle on all host cores,
+    one event per task; stops after the budget.  Returns (events/s, cores, n)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    cfg = oracle.default_config(zmx=zmx)
+    cores = os.cpu_count() or 1
+    events = list(range(batch.n_events)) if events is None else list(events)
+
+    def one(e):
+        x, zone = batch.hits_of(e)
+        s = oracle.seeding_event(cfg, x, zone)["seeds"]
+        st = np.stack([s["x_s"], s["y_s"], s["tx_s"], s["ty_s"]], 1)
+        oracle.matching_event(cfg, batch.velo_of(e), st)
+        return 1
+
+    done = 0
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        chunk = cores * 4
+        i = 0
+        while time.perf_counter() - t0 < budget_s:
+            sel = [events[(i + k) % len(events)] for k in range(chunk)]
+            done += sum(ex.map(one, sel))
+            i += chunk
+    dt = time.perf_counter() - t0
+    return done / dt, cores, done
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    from synth import calibrate_zmatch, make_workload
+    batch = make_workload(WORKLOAD)
+    zmx = calibrate_zmatch(7826.0)
+    vals = []
+    n_total = 0
+    for k in range(args.warmup + args.steps):
+        budget = 1.0 if k < args.warmup else max(2.0, min(10.0, 60.0 / max(1, args.steps)))
+        v, cores, n = time_oracle(batch, zmx, budget_s=budget)
+        if k >= args.warmup:
+            vals.append(v)
+            n_total += n
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 1000 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{WORKLOAD}: 1000 events, Poisson(150) tracks, 30% noise",
+                                            "events_per_step": 1000, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n_total} events of the workload, one event per task on {cores} threads"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--serve-rates", default="0.5", help="offered rates as fractions of batched capacity")
+    ap.add_argument("--per-event", type=int, default=200, help="events timed with per-event launches")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="batched measurement only (for profiling)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2606_14480_gb300 import st
+    from synth import calibrate_zmatch, make_workload
+
+    batch = make_workload(WORKLOAD, seed=1002 + rank)
+    n_ev = batch.n_events
+    zmx = calibrate_zmatch(7826.0)
+    cfg = st.st_config_default(zmx=zmx)
+    ctx = st.Context(cfg, device=local)
+    db = st.DeviceBatch.from_synth(batch, device=dev)
+    cap = max(1024, batch.n_hits // 4)
+    out = st.DeviceOutputs(n_ev, cap, device=dev)
+    ctx.st_reserve(n_ev, n_ev * db.max_hits, db.max_hits, cap)
+    ctx.st_set_timing(True)
+    stream = torch.cuda.Stream(device=dev)
+    graph = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    kernels_per_step = 5  # build, seed, scan, gather, match
+
+    # ---------------- batched: graph replay, inputs resident in HBM
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            graph.st_graph_launch(stream)
+        stream.synchronize()
+        ctx.st_read_counters(reset=True)
+        clocks = ClockSampler(local).start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        step_ms, kms = [], {"build": 0.0, "seed": 0.0, "gather": 0.0, "match": 0.0}
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ev0.record(stream)
+            graph.st_graph_launch(stream)
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            for k, v in ctx.st_kernel_ms().items():
+                kms[k] += v
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+    counters = ctx.st_read_counters(reset=True)
+    total_ms = float(np.sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * n_ev * args.steps / (total_ms / 1000.0)
+    ms_per_step = total_ms / args.steps
+
+    result = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32",
+              "data": "synthetic (seeded generator; Run-3-like occupancy)",
+              "config": {"workload": f"{WORKLOAD}: 1000 events, Poisson(150) tracks/event, 30% noise hits, "
+                                     f"{batch.n_hits / n_ev:.0f} hits/event, VELO truth + 20% ghosts",
+                         "events_per_step": n_ev, "mode": "batched: one CUDA graph of persistent kernels",
+                         "l2": "flushed between steps (256 MB write, untimed)",
+                         "seeds_per_event": counters["seeds"] / max(1, counters["events"])},
+              "gpu_launches": kernels_per_step * args.steps}
+    if clk:
+        result["clocks"] = clk
+
+    # ---------------- roofline of the seeding kernel
+    peaks, src = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    steps = args.steps
+    seed_ms = kms["seed"] / steps
+    units = {k: counters[k] / steps for k in ("pairs", "triplets", "ext_ok", "uv_init", "match_pairs")}
+    ops = (OPS_PER_UNIT["pairs"] * units["pairs"] + OPS_PER_UNIT["triplets"] * units["triplets"]
+           + OPS_PER_UNIT["fits"] * units["ext_ok"] + OPS_PER_UNIT["uv_init"] * units["uv_init"])
+    peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = ops / (seed_ms / 1000.0) / 1e12 if seed_ms > 0 else 0.0
+    traffic = traffic_from_profile("k_seed")
+    result["roofline"] = {"kernel": "k_seed", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                          "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                          "peak_source": f"FP32: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
+                                         f"({src} sm_max_mhz)",
+                          "kernel_ms": {k: v / steps for k, v in kms.items()},
+                          "units_per_launch": units,
+                          "hbm": {"algorithmic_bytes": None, "peak_gbs": float(peaks.get("hbm_gbs", 6800.0))}}
+    # algorithmic HBM bytes of one seeding launch: containers read (x) once,
+    # seed records written once
+    alg_bytes = 8.0 * batch.n_hits + 88.0 * counters["seeds"] / steps
+    result["roofline"]["hbm"]["algorithmic_bytes"] = alg_bytes
+    result["roofline"]["hbm"]["achieved_gbs"] = alg_bytes / (seed_ms / 1000.0) / 1e9 if seed_ms > 0 else 0.0
+
+    if args.quick:
+        graph.close()
+        ctx.close()
+        if rank == 0:
+            print(json.dumps(result), flush=True)
+        return
+
+    # ---------------- e2e through the public host API (pipeline)
+    ctx2 = st.Context(cfg, device=local)
+    ctx2.st_pipeline_configure(n_slots=2, max_events_per_slot=n_ev, max_hits_per_slot=batch.n_hits + 16,
+                               max_hits_per_event=db.max_hits, max_velo_per_event=1024)
+    hh, hv, keep = st.HostBuffers.inputs(batch.ev_off, batch.x, batch.zone, batch.velo_off, batch.velo)
+    hb = st.HostBuffers(n_ev, cap)
+    for _ in range(2):
+        t = ctx2.pipeline_submit(hh, hv)
+        ctx2.pipeline_poll(t, hb.seeds, hb.long, -1)
+    h2d = 8 * (n_ev + 1) * 2 + 8 * batch.n_hits + 16 * batch.velo.shape[0]
+    e2e_t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        t = ctx2.pipeline_submit(hh, hv)
+        rc, info = ctx2.pipeline_poll(t, hb.seeds, hb.long, -1)
+        e2e_t.append(time.perf_counter() - t0)
+    ns = int(hb.ev_off[-1])
+    d2h = 4 * (n_ev + 1) + 8 * n_ev + ns * (48 + 32 + 16 + 2 + 8)
+    e2e_total = float(np.sum(e2e_t))
+    if ws > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    result["e2e"] = {"value": ws * n_ev * args.steps / e2e_total, "unit": "events/s",
+                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                     "api": "pipeline_submit + pipeline_poll, host buffers, one batch in flight"}
+
+    if rank == 0 and ws == 1:
+        # ---------------- plain per-event launch
+        pe = min(args.per_event, n_ev)
+        ctx3 = st.Context(cfg, device=local)
+        ctx3.st_reserve(1, db.max_hits, db.max_hits, 512)
+        outs = st.DeviceOutputs(1, 512, device=dev)
+        import ctypes as C
+
+        def ev_struct(e):
+            h = st.StHits(1, db.ev_off.data_ptr() + 8 * e, db.x.data_ptr(), db.zone.data_ptr(), None, None,
+                          db.max_hits, 0)
+            v = st.StVelo(1, db.velo_off.data_ptr() + 8 * e, db.velo.data_ptr())
+            return h, v
+
+        with torch.cuda.stream(stream):
+            for e in range(3):
+                h, v = ev_struct(e)
+                ctx3.seeding_run(h, outs.seeds, stream)
+                ctx3.matching_run(v, outs.seeds, outs.long, stream)
+            stream.synchronize()
+            structs = [ev_struct(e) for e in range(pe)]
+            ev0.record(stream)
+            for h, v in structs:
+                ctx3.seeding_run(h, outs.seeds, stream)
+                ctx3.matching_run(v, outs.seeds, outs.long, stream)
+            ev1.record(stream)
+            ev1.synchronize()
+        pe_ms = ev0.elapsed_time(ev1)
+        result["per_event"] = {"value": pe / (pe_ms / 1000.0), "unit": "events/s", "events_timed": pe,
+                               "launches_per_event": kernels_per_step,
+                               "mode": "seeding_run + matching_run per event, one stream"}
+        del C
+        ctx3.close()
+
+        # ---------------- served: continuous batching of a Poisson request stream
+        result["served"] = serve(st, cfg, value, args, local)
+
+        # ---------------- CPU baseline: the oracle on the host cores
+        if not args.no_cpu_baseline:
+            v, cores, n = time_oracle(batch, zmx, budget_s=12.0)
+            result["cpu_baseline"] = {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
+                                      "sample": f"{n} events of the workload (cycled), seeding + matching, "
+                                                f"FP64, one event per task on {cores} threads, ~12 s"}
+    ctx2.close()
+    graph.close()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def serve(st, cfg, batched_rate, args, local):
+    """Poisson arrivals of request batches (sizes log-uniform 1-4096, events
+    from a pool with log-normal occupancy) at fractions of the batched rate."""
+    from synth import make_workload
+    from synth.events import poisson_arrivals, serving_requests
+    pool = make_workload("uneven", n_events=4096, seed=1005)
+    ctx = st.Context(cfg, device=local)
+    ctx.st_pipeline_configure(n_slots=4, max_events_per_slot=4096, max_hits_per_slot=int(pool.n_hits) + 16,
+                              max_hits_per_event=int(np.max(np.diff(pool.ev_off))), max_velo_per_event=4096)
+    out = {}
+    for frac in [float(f) for f in args.serve_rates.split(",")]:
+        rate = frac * batched_rate  # events/s offered
+        sizes = serving_requests(int(rate * args.serve_seconds) + 1, seed=1005)
+        n_req = len(sizes)
+        mean = float(np.mean(sizes))
+        arr = poisson_arrivals(n_req, rate / mean, seed=1006)
+        starts = np.cumsum(np.concatenate([[0], sizes[:-1]])) % pool.n_events
+        reqs = []
+        for s0, n in zip(starts, sizes):
+            idx = (np.arange(n) + s0) % pool.n_events
+            sub = pool.subset(idx)
+            reqs.append(st.HostBuffers.inputs(sub.ev_off, sub.x, sub.zone, sub.velo_off, sub.velo))
+        lat = [None] * n_req
+        tickets = [None] * n_req
+        done = threading.Event()
+
+        def poller():
+            for i in range(n_req):
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                hb = st.HostBuffers(int(sizes[i]), int(sizes[i]) * 300 + 64)
+                rc, info = ctx.pipeline_poll(tickets[i], hb.seeds, hb.long, -1)
+                lat[i] = (info.t_done_ns - info.t_submit_ns) / 1e6
+            done.set()
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            wait = arr[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            hits, velo, keep = reqs[i]
+            tickets[i] = ctx.pipeline_submit(hits, velo)
+        done.wait()
+        wall = time.perf_counter() - t0
+        lat_a = np.array(lat)
+        out[f"{frac:g}"] = {"offered_events_per_s": rate, "events_per_s": float(np.sum(sizes) / wall),
+                            "requests": n_req, "events": int(np.sum(sizes)),
+                            "p50_ms": float(np.percentile(lat_a, 50)), "p99_ms": float(np.percentile(lat_a, 99))}
+    ctx.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,284 @@
+/*
+ * st.h -- C ABI of libst: GB300 (sm_103a) SciFi Seeding and VELO-SciFi
+ * Matching, the hot path of the backward long-track reconstruction described
+ * in "Seeding and Matching algorithms for the first GPU-based High Level
+ * Trigger of the LHCb experiment" (Sections 3 and 4).
+ *
+ * Problem statement (Abstract, Section 4): from the hits of the SciFi tracker
+ * build T-track segments ("seeds"), then link each seed to the VELO segment
+ * whose straight-line extrapolation matches it best, forming a Long track.
+ *
+ * Conventions for every entry point
+ *  - Return value is an st_status; nothing aborts, traps or exits.
+ *  - Device pointers are owned by the caller (e.g. torch tensors) and are never
+ *    freed or retained beyond the call's stream work.  Host pointers are read
+ *    during the call only, unless stated otherwise.
+ *  - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *    void*; NULL = legacy default stream) and is asynchronous unless stated.
+ *  - Indices of hits are event-local: 0 .. hits-of-the-event-1, in the
+ *    caller's order.  Seeds and VELO states are likewise event-local.
+ *  - Per-event problems (invalid hit, capacity exceeded) are reported in the
+ *    per-event status array, never by writing out of bounds.
+ *  - A context is used by one host thread at a time, except the pipeline_*
+ *    calls, which are thread-safe.
+ */
+#ifndef ST_H
+#define ST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ST_OK = 0,
+    ST_PENDING = 1,     /* pipeline_poll: result not ready yet */
+    ST_EINVAL = -1,     /* invalid argument / input */
+    ST_ENOMEM = -2,     /* device or pinned allocation failed */
+    ST_OVERFLOW = -3,   /* a capacity was exceeded (per event, or call-level) */
+    ST_TIMEOUT = -4,    /* pipeline_poll: the wait ran out */
+    ST_ECUDA = -5,      /* a CUDA runtime call failed; see st_last_error */
+    ST_ESTATE = -6      /* call not valid in the context's current state */
+} st_status;
+
+#define ST_NLAYER 12
+
+/*
+ * Method parameters and launch tuning.  All geometry in mm.  Fill with
+ * st_config_default() and override fields.  Layers: 12 SciFi layers, three
+ * stations of four layers ordered x,u,v,x (Section 1); zone = 2*layer + half,
+ * half 1 holding the hits of particles at y >= 0 (Section 5.2).
+ */
+typedef struct {
+    double z[ST_NLAYER];       /* layer z */
+    double dxdy[ST_NLAYER];    /* tan of the stereo angle: 0 (x), +tan5 (u), -tan5 (v) */
+    double z_ref;              /* reference z of the track model, Eq. (trackequation) */
+    double d_ratio;            /* fixed cubic-correction coefficient of Eq. (trackequation) */
+    /* XZ seeding (Section 3.3) */
+    double invp_a, invp_b;     /* Eq. (invp): 1/p = a|x0| + b x0^2 (1/p in (MeV/c)^-1) */
+    double p_min;              /* MeV/c, both iterations (Section 3.2) */
+    double alpha0, alpha1;     /* Eq. (alphacorr), MeV/c */
+    double dx3_scale;          /* scales Delta x3^max of Eq. (tolHp); 1 = paper */
+    int32_t n_iter;            /* XZ iterations (2 in HLT1) */
+    int32_t iter_layers[2][3]; /* initial x-layers (T1, T2, T3) of each iteration */
+    int32_t pad0;
+    double kappa_c;            /* third-hit band centre: -sign(x0)*c_x = kappa_c * (1/p) */
+    double m_lo, m_hi;         /* band edges as multiples of the centre */
+    double c_nsigma;           /* band widening, in units of the c_x resolution */
+    double sigma_x;            /* x resolution (mm) used in the band and in chi2_x */
+    double ext_tol;            /* x-layer extension tolerance (Section 3.2): 1 mm */
+    double chi2x_max;          /* x-z fit cut on chi2/ndf */
+    double score_w_chi2;       /* Eq. (seed_clone_score): 1000 */
+    double score_w5;           /* Eq. (seed_clone_score): 10 for five-hit tracks */
+    /* UV seeding (Section 3.4) */
+    int32_t uv_init[2];        /* initial stereo layer of pass A and pass B */
+    int32_t n_uv_min;          /* stereo hits a seed needs (2..6) */
+    int32_t pad1;
+    double uv_tol;             /* closest stereo hit within 2 mm */
+    double uv_y_overlap;       /* first-layer window reaches this far into the other half */
+    double uv_y_max;           /* |y| limit of the first-layer window */
+    double sigma_y;            /* y resolution used in chi2_y */
+    double z_state;            /* z of the seed state handed to matching */
+    /* Matching (Section 4) */
+    double z_velo;             /* z of the VELO states */
+    double z_match_y;          /* y matching plane: 10 m */
+    double zmx[5];             /* A_x..E_x of Eq. (z_match) */
+    double presel[4];          /* |dx|, |dy|, |dtx|, |dty| preselection cuts (Section 4.2) */
+    double presel_scale;       /* multiplies the four preselection cuts */
+    double tol_scale;          /* multiplies tol_x, tol_y, tol_tx, tol_ty */
+    double tolx[3];            /* tol_x = tolx0 (tolx1^2 + tolx2^2 dtx^2) */
+    double toly[3];            /* tol_y = toly0 (toly1^2 + toly2^2 (tx^2 + ty^2)) */
+    double tol_tx, tol_ty;
+    double chi2_match_max;     /* chi2_match < 2 */
+    int32_t velo_unique;       /* 1: a VELO segment keeps only its best seed */
+    /* launch tuning (no effect on results) */
+    int32_t threads_seed;      /* threads per CTA of the seeding kernel: 64, 128, 256, 512 */
+    int32_t threads_build;     /* threads per CTA of the container kernel */
+    int32_t threads_match;     /* threads per CTA of the matching kernel */
+    int32_t ctas_per_sm;       /* persistent CTAs per SM (0 = occupancy maximum) */
+    int32_t smem_hits;         /* hits of one detector half staged in shared memory */
+    int32_t cand_cap;          /* x-z candidates per (event, half) work item */
+    int32_t pad2;
+} st_config;
+
+/* Hits of a batch of events (CSR).  All arrays are DEVICE memory.
+ * ev_off[n_events+1] (int64, non-decreasing) indexes x / zone / z / dxdy;
+ * ev_off[0] need not be 0.  z and dxdy may be NULL; when given, each hit's
+ * value must equal the configured value of its layer within 1e-3 mm / 1e-6,
+ * else the event's status is ST_EINVAL.  max_hits_per_event is a host-side
+ * bound; larger events get ST_OVERFLOW.  Events with a zone outside [0, 24)
+ * or a non-finite x get ST_EINVAL. */
+typedef struct {
+    int64_t n_events;
+    const int64_t* ev_off;
+    const float* x;
+    const int32_t* zone;
+    const float* z;
+    const float* dxdy;
+    int32_t max_hits_per_event;
+    int32_t pad;
+} st_hits;
+
+/* Seeding output (T tracks).  All arrays DEVICE memory, caller-allocated.
+ *   ev_off  [n_events+1] int32: seeds of event e are [ev_off[e], ev_off[e+1])
+ *   hits    [cap*12]     int32: event-local hit index per layer, -1 = none
+ *   params  [cap*8]      float: a, b, c (x-z model), chi2_x, y0, ty, chi2_y, 0
+ *   state   [cap*4]      float: x, y, tx, ty at z_state
+ *   n_hits  [cap*2]      int8 : x-layer hits, stereo hits
+ *   status  [n_events]   int32: ST_OK, ST_EINVAL or ST_OVERFLOW
+ * Within an event, seeds of half 0 precede those of half 1, each in the
+ * deterministic order of the search (iteration, T1 hit, T3 hit, T2 hit). */
+typedef struct {
+    int64_t cap;
+    int32_t* ev_off;
+    int32_t* hits;
+    float* params;
+    float* state;
+    int8_t* n_hits;
+    int32_t* status;
+} st_seeds;
+
+/* VELO segments (CSR), DEVICE memory: state[4*i] = x, y, tx, ty at z_velo. */
+typedef struct {
+    int64_t n_events;
+    const int64_t* ev_off;
+    const float* state;
+} st_velo;
+
+/* Matching output, one entry per seed (same indexing as st_seeds), DEVICE:
+ *   velo_idx [cap] int32: event-local VELO index of the Long track, -1 = none
+ *   chi2     [cap] float: chi2_match of that pair (0 if none)
+ *   n_long   [n_events] int32 (may be NULL): Long tracks per event */
+typedef struct {
+    int32_t* velo_idx;
+    float* chi2;
+    int32_t* n_long;
+} st_long;
+
+/* Per-stage work counters, summed over the calls since the last reset. */
+typedef struct {
+    int64_t pairs, triplets, ext_ok, cands, kept, uv_init, uv_cands, seeds;
+    int64_t match_pairs, match_presel, matched;
+    int64_t hits, events;
+} st_counters;
+
+typedef struct st_ctx st_ctx;
+typedef struct st_graph st_graph;
+
+/* Fill *cfg with the paper's constants (Sections 3-4), this library's
+ * readings of the values the paper leaves open, and default tuning. */
+void st_config_default(st_config* cfg);
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * Validates cfg (ST_EINVAL), derives the device constants and allocates the
+ * counters.  Scratch memory is allocated on first use or by st_reserve.
+ * *out receives the context; destroy it with st_destroy. */
+int st_create(const st_config* cfg, int device, st_ctx** out);
+
+/* Waits for the context's pipeline work, frees its memory and the context.
+ * NULL is accepted. */
+void st_destroy(st_ctx* ctx);
+
+/* Message of the last failing call on this context (owned by the context,
+ * valid until the next call).  Never NULL. */
+const char* st_last_error(const st_ctx* ctx);
+
+/* Pre-allocate scratch for batches of up to n_events events, n_hits hits,
+ * max_hits_per_event hits per event and seeds_cap seeds, so that later
+ * seeding_run / matching_run calls allocate nothing (required before CUDA
+ * graph capture).  Synchronous. */
+int st_reserve(st_ctx* ctx, int64_t n_events, int64_t n_hits, int32_t max_hits_per_event,
+               int64_t seeds_cap);
+
+/* SciFi Seeding (Section 3): per event, hit containers sorted by (layer
+ * zone, x); two XZ iterations of two-hit (Eqs. tolHp, alphacorr) and
+ * three-hit (Section 3.3.3) searches; extension to the other x-layers
+ * (1 mm) keeping >= 5 hits; least-squares x-z fit with d_ratio fixed and a
+ * chi2/ndf cut; O(n) clone killing (Eq. seed_clone_score and the two-pass
+ * vote of Section 3.3.4); iterative UV seeding (Section 3.4).
+ * Output `seeds` as described at st_seeds.  Returns ST_EINVAL for a bad
+ * argument (NULL array, cap < 0, n_events < 0), ST_ENOMEM / ST_ECUDA for
+ * allocation or launch failures; per-event problems go to seeds->status.
+ * Allocates scratch if st_reserve was not called for this size. */
+int seeding_run(st_ctx* ctx, const st_hits* hits, st_seeds* seeds, void* cuda_stream);
+
+/* VELO-SciFi Matching (Section 4): for every seed, every VELO segment of
+ * the same event is extrapolated with the seed to the kink plane z_match_x
+ * (Eq. z_match) and to z_match_y; pairs passing the preselection (Section
+ * 4.2) get chi2_match; the seed's Long track is the pair with the lowest
+ * chi2_match below chi2_match_max (ties: lower VELO index).  `seeds` must be
+ * a seeding_run output for the same events (velo->n_events events).  The
+ * UT-hit search and the ghost network of Sections 4.3-4.4 are not part of
+ * this call.  Errors as seeding_run. */
+int matching_run(st_ctx* ctx, const st_velo* velo, const st_seeds* seeds, st_long* out,
+                 void* cuda_stream);
+
+/* Capture seeding_run + matching_run for these exact buffers and sizes into a
+ * CUDA graph (persistent, work-queue kernels).  Scratch must be reserved
+ * first (st_reserve).  The arguments' pointers must stay valid while the
+ * graph exists.  *out receives the graph; launch with st_graph_launch. */
+int st_graph_create(st_ctx* ctx, const st_hits* hits, const st_velo* velo, st_seeds* seeds,
+                    st_long* out, st_graph** graph);
+int st_graph_launch(st_graph* graph, void* cuda_stream);
+void st_graph_destroy(st_graph* graph);
+
+/* Kernel timing (a tracing aid).  When enabled, seeding_run, matching_run
+ * and graphs created afterwards record CUDA events around each kernel on the
+ * launch stream.  st_kernel_ms waits for the last recorded work and returns
+ * the durations (ms) of its kernels: [0] hit containers, [1] seeding,
+ * [2] seed gather, [3] matching (0 for kernels not run). */
+int st_set_timing(st_ctx* ctx, int enable);
+int st_kernel_ms(st_ctx* ctx, float ms[4]);
+
+/* Counters of the work done since the last reset (synchronises the device).
+ * reset != 0 zeroes them afterwards. */
+int st_read_counters(st_ctx* ctx, st_counters* out, int reset);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of host-side event batches.                */
+/* ---------------------------------------------------------------------- */
+
+/* Serving limits; set before the first pipeline_submit. */
+typedef struct {
+    int32_t n_slots;             /* batches in flight on the device (streams) */
+    int32_t max_events_per_slot; /* events packed into one launch */
+    int64_t max_hits_per_slot;   /* hits packed into one launch */
+    int32_t max_hits_per_event;
+    int32_t max_velo_per_event;
+    int64_t mem_cap_bytes;       /* device + pinned memory the pipeline may hold */
+} st_pipeline_config;
+
+void st_pipeline_config_default(st_pipeline_config* pc);
+int st_pipeline_configure(st_ctx* ctx, const st_pipeline_config* pc);
+
+/* Queue one batch given in HOST memory (hits->x, zone, ev_off etc. and
+ * velo->state, ev_off are host pointers; z/dxdy ignored).  The data are
+ * copied before the call returns, so the caller may reuse its buffers.
+ * Batches are admitted to the device as slots and memory free up, packed with
+ * other waiting batches into one launch, and overlap on the device.
+ * *ticket identifies the batch.  ST_OVERFLOW if the batch can never fit a
+ * slot; ST_ESTATE after st_destroy has begun. */
+int pipeline_submit(st_ctx* ctx, const st_hits* host_hits, const st_velo* host_velo,
+                    uint64_t* ticket);
+
+/* Timing of a finished request (host steady clock, nanoseconds). */
+typedef struct {
+    int64_t t_submit_ns, t_launch_ns, t_done_ns;
+    int32_t n_events, n_seeds;
+} st_request_info;
+
+/* Wait up to timeout_us (0 = do not wait, < 0 = forever) for the batch of
+ * `ticket`.  On ST_OK its seeds and Long tracks are copied into the HOST
+ * buffers host_seeds (cap, ev_off, hits, params, state, n_hits, status) and
+ * host_long (velo_idx, chi2, n_long; may be NULL), info (may be NULL) is
+ * filled, and the ticket is released.  ST_PENDING (timeout_us == 0) or
+ * ST_TIMEOUT if not ready; ST_OVERFLOW if host_seeds->cap is too small
+ * (ticket kept); ST_EINVAL for an unknown ticket. */
+int pipeline_poll(st_ctx* ctx, uint64_t ticket, st_seeds* host_seeds, st_long* host_long,
+                  int64_t timeout_us, st_request_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

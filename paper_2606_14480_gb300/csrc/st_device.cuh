@@ -1,0 +1,180 @@
+// st_device.cuh -- device-side constants and helpers of libst (sm_103a).
+//
+// DevParams holds every constant the kernels need, derived once on the host
+// in double precision from st_config and rounded to float (float-float pairs
+// where a value enters a compensated computation).  It is passed by value as a
+// __grid_constant__ kernel parameter.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace st {
+
+constexpr int kLayers = 12;
+constexpr int kZones = 24;
+constexpr int kSlotsPerHalf = 12;  // 6 x-layer zones, then 6 stereo zones
+constexpr int kZoffStride = 25;    // per event: 24 slot starts + end
+constexpr int kMasks = 7;          // x-layer hit patterns with >= 5 hits
+constexpr int kMaxThreads = 512;
+
+// Container order of an event: half-major; within a half the x-layers
+// (0,3,4,7,8,11) then the stereo layers (1,2,5,6,9,10), each sorted by x.
+// slot(zone) = 12*half + (x-slot or 6 + stereo slot).
+
+struct IterP {
+    int s1, s2, s3;        // x-slots of the initial layers T1, T2, T3
+    int ext[3];            // x-slots of the other three x-layers, ascending
+    float scale3;          // (z3 + alpha_corr) / z1
+    float dx3;             // Delta x3^max
+    float inv_dz31;        // 1 / (z3 - z1)
+    float dz21;            // z2 - z1
+    float z1;
+    float k3, inv_k3;      // chord deviation per unit c_x at z2
+    float c0;              // band widening in c_x units
+    float mlo_k, mhi_k;    // m_lo * kappa_c, m_hi * kappa_c
+    float q31;             // (f3 - f1) / (z3 - z1)
+    float zb1, f1;         // zb and f of T1
+};
+
+struct DevParams {
+    // x-slot geometry: zb = z - z_ref (exact), f = zb^2 (1 + d zb) as hi + lo
+    float xzb[6], xf_hi[6], xf_lo[6];
+    // stereo-slot geometry (slots ordered by z)
+    float uz[6], uzb[6], uf_hi[6], uf_lo[6], ut[6], uzt[6];
+    float zc_uv;           // centring z of the y-z line fit (uzt = uz - zc_uv)
+    IterP it[2];
+    int n_iter;
+    float invp_a, invp_b;
+    float ext_tol, chi2x_max, inv_sx2, w_chi2, w5;
+    float G[kMasks][3][6]; // least-squares gain per x-hit pattern
+    int mask_index[64];    // 6-bit x-hit pattern -> G index, -1 if < 5 hits
+    int uv_init[2];        // stereo slot of the initial layer of each pass
+    int uv_rem[2][5];      // the other stereo slots of each pass, ascending z
+    int n_uv_min;
+    float uv_tol;
+    float uv_ylo[2], uv_yhi[2];  // first-layer y window per half
+    float inv_sy2;
+    // seed state
+    float zS, zbS, fS, dfS;
+    // matching
+    float zV, zMY;
+    float A_hi, A_lo, Bx, Cx, Dx, Ex;
+    float dAV_hi, dAV_lo;  // A - z_velo
+    float dAS_hi, dAS_lo;  // A - z_state
+    float dMV_hi, dMV_lo;  // z_match_y - z_velo
+    float dMS_hi, dMS_lo;  // z_match_y - z_state
+    float cut_x, cut_y, cut_tx, cut_ty;
+    float tolx_a, tolx_b, toly_a, toly_b, inv_toltx, inv_tolty, chi2m_max;
+    int velo_unique;
+    // per layer, for the optional z / dxdy input check
+    float zl[12], tl[12];
+    int slot_of_zone[24];
+};
+
+// ---------------------------------------------------------------------------
+// error-free transformations (Knuth's TwoSum, FMA-based TwoProduct)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// ---------------------------------------------------------------------------
+// searches over an ascending float array
+// ---------------------------------------------------------------------------
+
+// first index i in [0, n) with a[i] >= v (n if none)
+__device__ __forceinline__ int lower_bound_f(const float* a, int n, float v) {
+    int lo = 0, len = n;
+    while (len > 0) {
+        int h = len >> 1;
+        if (a[lo + h] < v) {
+            lo += h + 1;
+            len -= h + 1;
+        } else {
+            len = h;
+        }
+    }
+    return lo;
+}
+
+// first index i in [0, n) with a[i] > v (n if none)
+__device__ __forceinline__ int upper_bound_f(const float* a, int n, float v) {
+    int lo = 0, len = n;
+    while (len > 0) {
+        int h = len >> 1;
+        if (!(v < a[lo + h])) {
+            lo += h + 1;
+            len -= h + 1;
+        } else {
+            len = h;
+        }
+    }
+    return lo;
+}
+
+// largest t in [0, n) with s[t] <= p, for a non-decreasing int array s with
+// s[0] = 0 <= p (the owner of item p in a load-balanced expansion)
+__device__ __forceinline__ int owner_of(const int* s, int n, int p) {
+    int lo = 0, len = n;
+    while (len > 0) {
+        int h = len >> 1;
+        if (s[lo + h] <= p) {
+            lo += h + 1;
+            len -= h + 1;
+        } else {
+            len = h;
+        }
+    }
+    return lo - 1;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan of one int per thread; returns the exclusive
+// prefix, writes the block total.  `tmp` holds >= 33 ints of shared memory.
+// Contains __syncthreads(); every thread of the block must call it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int block_exscan(int v, int* tmp, int& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < nw ? tmp[lane] : 0;
+        int ww = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, ww, o);
+            if (lane >= o) ww += y;
+        }
+        if (lane < nw) tmp[lane] = ww - w;
+        if (lane == 31) tmp[32] = ww;
+    }
+    __syncthreads();
+    int res = x - v + tmp[wid];
+    total = tmp[32];
+    __syncthreads();
+    return res;
+}
+
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace st

@@ -1,0 +1,977 @@
+// st_kernels.cu -- sm_103a kernels of the SciFi Seeding + VELO-SciFi Matching
+// hot path.  All kernels are persistent: a grid of (SMs x resident CTAs) pulls
+// work items (events, or detector halves of events) from a device counter.
+//
+//   k_build   one event per item: validate hits, sort them by (container
+//             slot, x, index) with a bucketed rank sort in shared memory, write
+//             the per-event container (x, original index) and slot offsets.
+//   k_seed    one detector half of one event per item (the paper keeps the
+//             halves apart, Section 5.2): XZ seeding of both iterations with
+//             load-balanced expansion of pairs and triplets, extension and
+//             compensated least-squares fit, O(n) clone killing with a 64-bit
+//             atomicMin table, iterative UV seeding with a 64-bit atomicMin
+//             per seed, and the seed records.
+//   k_scan / k_gather   per-event CSR of the seed records.
+//   k_match   one event per item: VELO x seed grid, warp argmin per seed.
+#include <algorithm>
+#include <cfloat>
+
+#include "st_kernels.cuh"
+
+namespace st {
+
+typedef unsigned long long ull;
+
+__constant__ int kXLayer[6] = {0, 3, 4, 7, 8, 11};
+__constant__ int kULayer[6] = {1, 2, 5, 6, 9, 10};
+
+static __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// First container index of event e: events are laid out back to back with
+// three spare entries each, rounded up to a multiple of four floats so that
+// every event starts 16-byte aligned.
+__device__ __forceinline__ int64_t cont_base(const int64_t* ev_off, int64_t e) {
+    int64_t b = (ev_off[e] - ev_off[0]) + 3 * e;
+    return (b + 3) & ~int64_t(3);
+}
+
+__device__ __forceinline__ void flush_counters(unsigned long long* dst, const ull* c, int n) {
+    for (int k = 0; k < n; ++k) {
+        ull v = c[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst + k, v);
+    }
+}
+
+// ===========================================================================
+// container build
+// ===========================================================================
+
+constexpr float kBinRange = 3500.f;
+
+size_t build_smem_bytes(int bins, int smem_hits) {
+    const int NB = kZones * bins;
+    return align16(sizeof(int) * (2 * NB + 1 + 36)) + align16(size_t(10) * smem_hits);
+}
+
+__global__ void __launch_bounds__(kMaxThreads)
+k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int B = A.bins, NB = kZones * B, T = blockDim.x, tid = threadIdx.x;
+    int* cnt = reinterpret_cast<int*>(smem);
+    int* off = cnt + NB;
+    int* tmp = off + NB + 1;
+    unsigned char* harea = smem + align16(sizeof(int) * (2 * NB + 1 + 36));
+    __shared__ int s_item, s_bad;
+    ull ctr[2] = {0, 0};
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int64_t e = s_item;
+        if (e >= A.n_events) break;
+        const int64_t h0 = A.ev_off[e];
+        const int64_t n64 = A.ev_off[e + 1] - h0;
+        int32_t* zo = A.zoff + e * kZoffStride;
+        if (n64 < 0 || n64 > A.max_hits) {
+            for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
+            if (tid == 0) A.status[e] = -3;  // ST_OVERFLOW
+            continue;
+        }
+        const int n = static_cast<int>(n64);
+        const int64_t cb = cont_base(A.ev_off, e);
+        if (cb + n > A.cont_cap) {  // an earlier oversized event pushed this one past the container
+            for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
+            if (tid == 0) A.status[e] = -3;  // ST_OVERFLOW
+            continue;
+        }
+        const bool in_smem = n <= A.smem_hits;
+        unsigned char* base = in_smem ? harea : A.big + int64_t(blockIdx.x) * A.big_stride;
+        const int cap = in_smem ? A.smem_hits : A.max_hits;
+        float* hx = reinterpret_cast<float*>(base);
+        uint16_t* bk = reinterpret_cast<uint16_t*>(hx + cap);
+        uint16_t* rk = bk + cap;
+        uint16_t* pm = rk + cap;
+        for (int k = tid; k < NB; k += T) cnt[k] = 0;
+        if (tid == 0) s_bad = 0;
+        __syncthreads();
+        const float binscale = B / (2.f * kBinRange);
+        for (int i = tid; i < n; i += T) {
+            const float x = A.x[h0 + i];
+            const int zn = A.zone[h0 + i];
+            bool bad = !(zn >= 0 && zn < kZones) || !isfinite(x);
+            if (!bad) {
+                const int L = zn >> 1;
+                if (A.z && !(fabsf(A.z[h0 + i] - P.zl[L]) <= 1e-3f)) bad = true;
+                if (A.dxdy && !(fabsf(A.dxdy[h0 + i] - P.tl[L]) <= 1e-6f)) bad = true;
+            }
+            if (bad) {
+                s_bad = 1;
+                continue;
+            }
+            int bin = __float2int_rd((x + kBinRange) * binscale);
+            bin = min(max(bin, 0), B - 1);
+            const int b = P.slot_of_zone[zn] * B + bin;
+            hx[i] = x;
+            bk[i] = static_cast<uint16_t>(b);
+            rk[i] = static_cast<uint16_t>(atomicAdd(&cnt[b], 1));
+        }
+        __syncthreads();
+        if (s_bad) {
+            for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
+            if (tid == 0) A.status[e] = -1;  // ST_EINVAL
+            continue;
+        }
+        {   // exclusive scan of the bucket counts
+            const int per = (NB + T - 1) / T;
+            const int k0 = min(tid * per, NB), k1 = min(k0 + per, NB);
+            int sum = 0;
+            for (int k = k0; k < k1; ++k) sum += cnt[k];
+            int tot;
+            int ex = block_exscan(sum, tmp, tot);
+            for (int k = k0; k < k1; ++k) {
+                off[k] = ex;
+                ex += cnt[k];
+            }
+            if (tid == 0) off[NB] = tot;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += T) pm[off[bk[i]] + rk[i]] = static_cast<uint16_t>(i);
+        __syncthreads();
+        for (int i = tid; i < n; i += T) {
+            const int b = bk[i], s = off[b], c = cnt[b];
+            const float x = hx[i];
+            int r = 0;
+            for (int k = s; k < s + c; ++k) {
+                const int j = pm[k];
+                const float xj = hx[j];
+                r += (xj < x) || (xj == x && j < i);
+            }
+            A.cx[cb + s + r] = x;
+            A.corig[cb + s + r] = i;
+        }
+        for (int k = tid; k < kZoffStride; k += T) zo[k] = off[k * B];
+        if (tid == 0) {
+            A.status[e] = 0;
+            ctr[0] += n;
+            ctr[1] += 1;
+        }
+    }
+    flush_counters(A.counters + C_HITS, ctr, 2);
+}
+
+// ===========================================================================
+// seeding
+// ===========================================================================
+
+struct Trip {
+    int pos[6];
+    float th[3], dth[3];
+    float chi2, score;
+    int nx;
+};
+
+// Triplet -> exact 3-hit model, extension to the other x-layers (closest hit
+// within ext_tol, ties to the smaller x), least-squares fit and chi2 cut.
+// The fit is done on residuals y_j of the hits from the 3-hit model, formed
+// with error-free transformations so that they keep ~1e-7 mm accuracy; the
+// correction dth = G y and the chi2 are then computed from small numbers.
+// Returns 0 (fewer than 5 hits), 1 (chi2 cut) or 2 (candidate).
+__device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, const int* szl,
+                          int k1, int k2, int k3, Trip& o) {
+    const int p1 = szl[I.s1] + k1, p2 = szl[I.s2] + k2, p3 = szl[I.s3] + k3;
+    const float x1 = X[p1], x2 = X[p2], x3 = X[p3];
+    const float t13 = (x3 - x1) * I.inv_dz31;
+    const float base = fmaf(I.dz21, t13, x1);
+    const float c3 = (x2 - base) * I.inv_k3;
+    const float b3 = fmaf(-c3, I.q31, t13);
+    const float a3 = x1 - fmaf(c3, I.f1, b3 * I.zb1);
+#pragma unroll
+    for (int s = 0; s < 6; ++s) o.pos[s] = -1;
+    o.pos[I.s1] = p1;
+    o.pos[I.s2] = p2;
+    o.pos[I.s3] = p3;
+    int nx = 3;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int s = I.ext[j];
+        const float xp = fmaf(c3, P.xf_hi[s], fmaf(b3, P.xzb[s], a3));
+        const int st = szl[s], n = szl[s + 1] - st;
+        int k = lower_bound_f(X + st, n, xp - P.ext_tol);
+        int best = -1;
+        float bd = 0.f;
+        for (; k < n; ++k) {
+            const float xh = X[st + k];
+            if (xh > xp + P.ext_tol) break;
+            const float d = fabsf(xh - xp);
+            if (d <= P.ext_tol && (best < 0 || d < bd)) {
+                best = st + k;
+                bd = d;
+            }
+        }
+        if (best >= 0) {
+            o.pos[s] = best;
+            ++nx;
+        }
+    }
+    if (nx < 5) return 0;
+    int m = 0;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) m |= (o.pos[s] >= 0) << s;
+    const int mi = P.mask_index[m];
+    float y[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        y[s] = 0.f;
+        if (o.pos[s] >= 0) {
+            float d, e;
+            two_sum(X[o.pos[s]], -a3, d, e);
+            float v = fmaf(-b3, P.xzb[s], d);
+            v = fmaf(-c3, P.xf_hi[s], v);
+            y[s] = v + fmaf(-c3, P.xf_lo[s], e);
+        }
+    }
+    float da = 0.f, db = 0.f, dc = 0.f;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        da = fmaf(P.G[mi][0][s], y[s], da);
+        db = fmaf(P.G[mi][1][s], y[s], db);
+        dc = fmaf(P.G[mi][2][s], y[s], dc);
+    }
+    float chi2 = 0.f;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        if (o.pos[s] >= 0) {
+            const float r = y[s] - fmaf(dc, P.xf_hi[s], fmaf(db, P.xzb[s], da));
+            chi2 = fmaf(r, r, chi2);
+        }
+    }
+    chi2 *= P.inv_sx2;
+    if (chi2 / static_cast<float>(nx - 3) > P.chi2x_max) return 1;
+    o.th[0] = a3; o.th[1] = b3; o.th[2] = c3;
+    o.dth[0] = da; o.dth[1] = db; o.dth[2] = dc;
+    o.chi2 = chi2;
+    o.nx = nx;
+    const float sc = fmaf(P.w_chi2, chi2, fabsf(c3 + dc));
+    o.score = nx == 6 ? sc : P.w5 * sc;
+    return 2;
+}
+
+// x(z) of a seed at stereo slot u (3-hit model plus fit correction)
+__device__ __forceinline__ float x_at_uv(const DevParams& P, const float* th, const float* dth, int u) {
+    return fmaf(th[2], P.uf_hi[u], fmaf(th[1], P.uzb[u], th[0])) +
+           fmaf(dth[2], P.uf_hi[u], fmaf(dth[1], P.uzb[u], dth[0]));
+}
+
+struct UV {
+    int pos[6];
+    int n;
+    float chi2, tyr, beta, wm, zm;
+};
+
+// One UV combination (Section 3.4): start from the kinit-th hit of the
+// initial stereo layer of `pass`, ty from the origin, closest hit within
+// uv_tol in each remaining stereo layer in increasing z with ty averaging,
+// then (fit = true, n >= n_uv_min) the straight-line fit y = y0 + ty z.  The
+// y of each hit is formed as a float-float from error-free transformations
+// and fitted relative to the line y = tyr z, so chi2_y keeps ~1e-6 relative
+// accuracy.
+__device__ void uv_combo(const DevParams& P, const float* X, const int* szl, const float* th,
+                         const float* dth, int pass, int kinit, bool fit, UV& o) {
+#pragma unroll
+    for (int u = 0; u < 6; ++u) o.pos[u] = -1;
+    const int ui = P.uv_init[pass];
+    const int pi = szl[6 + ui] + kinit;
+    o.pos[ui] = pi;
+    const float yi = (x_at_uv(P, th, dth, ui) - X[pi]) / P.ut[ui];
+    float ty = yi / P.uz[ui];
+    int n = 1;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int u = P.uv_rem[pass][q];
+        const float Xl = x_at_uv(P, th, dth, u);
+        const float xp = Xl - P.ut[u] * ty * P.uz[u];
+        const int st = szl[6 + u], nn = szl[7 + u] - st;
+        int k = lower_bound_f(X + st, nn, xp - P.uv_tol);
+        int best = -1;
+        float bd = 0.f;
+        for (; k < nn; ++k) {
+            const float xh = X[st + k];
+            if (xh > xp + P.uv_tol) break;
+            const float d = fabsf(xh - xp);
+            if (d <= P.uv_tol && (best < 0 || d < bd)) {
+                best = st + k;
+                bd = d;
+            }
+        }
+        if (best >= 0) {
+            const float yl = (Xl - X[best]) / P.ut[u];
+            ty = 0.5f * (ty + yl / P.uz[u]);
+            o.pos[u] = best;
+            ++n;
+        }
+    }
+    o.n = n;
+    o.chi2 = 0.f;
+    o.tyr = ty;
+    o.beta = 0.f;
+    o.wm = 0.f;
+    o.zm = 0.f;
+    if (!fit || n < P.n_uv_min) return;
+    float w[6], zt[6];
+    float sw = 0.f, sz = 0.f;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+        w[u] = 0.f;
+        zt[u] = P.uzt[u];
+        if (o.pos[u] < 0) continue;
+        const float xh = X[o.pos[u]];
+        // D = x(z_u) - x_hit as hi + lo
+        float s, e, p, pe, s2, e2, p2, pe2, s3, e3;
+        two_sum(th[0], -xh, s, e);
+        two_prod(th[1], P.uzb[u], p, pe);
+        two_sum(s, p, s2, e2);
+        two_prod(th[2], P.uf_hi[u], p2, pe2);
+        two_sum(s2, p2, s3, e3);
+        const float lo = ((e + pe) + (e2 + pe2)) + (e3 + fmaf(th[2], P.uf_lo[u],
+                          fmaf(dth[2], P.uf_hi[u], fmaf(dth[1], P.uzb[u], dth[0]))));
+        // y = D / t
+        const float t = P.ut[u];
+        const float yh = s3 / t;
+        const float rem = fmaf(-yh, t, s3);
+        const float yl = (rem + lo) / t;
+        w[u] = fmaf(-ty, P.uz[u], yh) + yl;
+        sw += w[u];
+        sz += zt[u];
+    }
+    const float inv_n = 1.f / static_cast<float>(n);
+    const float wm = sw * inv_n, zm = sz * inv_n;
+    float szz = 0.f, szw = 0.f;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+        if (o.pos[u] < 0) continue;
+        const float dz = zt[u] - zm;
+        szz = fmaf(dz, dz, szz);
+        szw = fmaf(dz, w[u] - wm, szw);
+    }
+    const float beta = szw / szz;
+    float chi2 = 0.f;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+        if (o.pos[u] < 0) continue;
+        const float r = (w[u] - wm) - beta * (zt[u] - zm);
+        chi2 = fmaf(r, r, chi2);
+    }
+    o.chi2 = chi2 * P.inv_sy2;
+    o.beta = beta;
+    o.wm = wm;
+    o.zm = zm;
+}
+
+__device__ __forceinline__ ull uv_key(int n, float chi2, int pass, int kinit) {
+    return (ull(6 - n) << 61) | (ull(__float_as_uint(chi2) & 0x7fffffffu) << 30) |
+           (ull(pass) << 29) | ull(kinit);
+}
+
+__device__ __forceinline__ ull pack_trip(int it, int k1, int k3, int k2) {
+    return (ull(it) << 60) | (ull(k1) << 40) | (ull(k3) << 20) | ull(k2);
+}
+
+size_t seed_smem_bytes(int threads, int smem_hits, int tbl_smem, int key_smem) {
+    return align16(sizeof(float) * smem_hits) + sizeof(ull) * (tbl_smem + key_smem) +
+           sizeof(ull) * 2 * threads + sizeof(int) * 7 * threads + sizeof(int) * (36 + 16);
+}
+
+size_t seed_slot_bytes(int cand_cap, int max_xhits) {
+    return align16(sizeof(int) * 16 * size_t(cand_cap)) + sizeof(ull) * (size_t(max_xhits) + cand_cap);
+}
+
+__global__ void __launch_bounds__(kMaxThreads)
+k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = blockDim.x, tid = threadIdx.x;
+    unsigned char* sp = smem;
+    float* sx = reinterpret_cast<float*>(sp);
+    sp += align16(sizeof(float) * A.smem_hits);
+    ull* stab = reinterpret_cast<ull*>(sp);
+    sp += sizeof(ull) * A.tbl_smem;
+    ull* skey = reinterpret_cast<ull*>(sp);
+    sp += sizeof(ull) * A.key_smem;
+    ull* fifo = reinterpret_cast<ull*>(sp);
+    sp += sizeof(ull) * 2 * T;
+    int* sPS = reinterpret_cast<int*>(sp);
+    int* sA = sPS + T;
+    int* sB = sA + T;
+    int* sTS = sB + T;
+    int* sTA = sTS + T;
+    int* sTB = sTA + T;
+    int* sTC = sTB + T;
+    int* tmp = sTC + T;
+    int* szl = tmp + 36;
+    __shared__ int s_item;
+    __shared__ ull s_start;
+
+    const int CC = A.cand_cap;
+    uint8_t* slot = A.slot + int64_t(blockIdx.x) * A.slot_stride;
+    int* c_pos = reinterpret_cast<int*>(slot);           // [6][CC]
+    float* c_f = reinterpret_cast<float*>(c_pos + 6 * CC);  // [8][CC]: th0..2, dth0..2, chi2, score
+    int* c_nx = reinterpret_cast<int*>(c_f + 8 * CC);
+    int* kept = c_nx + CC;
+    ull* g_tbl = reinterpret_cast<ull*>(slot + align16(sizeof(int) * 16 * size_t(CC)));
+    ull* g_key = g_tbl + A.max_xhits;
+
+    ull ctr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= 2 * A.n_events) break;
+        const int64_t e = item >> 1;
+        const int h = static_cast<int>(item & 1);
+        if (A.status[e] != 0) {
+            if (tid == 0) A.item_count[item] = 0;
+            continue;
+        }
+        const int32_t* zo = A.zoff + e * kZoffStride + 12 * h;
+        const int64_t cbh = cont_base(A.ev_off, e) + zo[0];
+        const int nh = zo[12] - zo[0];
+        if (tid <= 12) szl[tid] = zo[tid] - zo[0];
+        const float* X = A.cx + cbh;
+        if (nh <= A.smem_hits) {
+            for (int i = tid; i < nh; i += T) sx[i] = X[i];
+            X = sx;
+        }
+        __syncthreads();
+
+        // ------------------------------------------------------------ XZ
+        int ncand = 0, nfifo = 0;
+        auto flush = [&](int m) {
+            Trip o;
+            int code = -1;
+            if (tid < m) {
+                const ull tk = fifo[tid];
+                const int it = static_cast<int>(tk >> 60);
+                code = do_triplet(P, P.it[it], X, szl, static_cast<int>((tk >> 40) & 0xFFFFF),
+                                  static_cast<int>(tk & 0xFFFFF), static_cast<int>((tk >> 20) & 0xFFFFF), o);
+                ctr[2] += code >= 1;
+            }
+            int tot;
+            const int co = block_exscan(code == 2 ? 1 : 0, tmp, tot);
+            if (code == 2) {
+                const int ci = ncand + co;
+                if (ci < CC) {
+#pragma unroll
+                    for (int s = 0; s < 6; ++s) c_pos[s * CC + ci] = o.pos[s];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        c_f[q * CC + ci] = o.th[q];
+                        c_f[(3 + q) * CC + ci] = o.dth[q];
+                    }
+                    c_f[6 * CC + ci] = o.chi2;
+                    c_f[7 * CC + ci] = o.score;
+                    c_nx[ci] = o.nx;
+                }
+            }
+            ncand += tot;
+            const int rem = nfifo - m;
+            ull v = 0;
+            if (tid < rem) v = fifo[m + tid];
+            __syncthreads();
+            if (tid < rem) fifo[tid] = v;
+            nfifo = rem;
+            __syncthreads();
+        };
+
+        const int n1_0 = szl[P.it[0].s1 + 1] - szl[P.it[0].s1];
+        const int n1_1 = P.n_iter > 1 ? szl[P.it[1].s1 + 1] - szl[P.it[1].s1] : 0;
+        const int n_items = n1_0 + n1_1;
+        for (int b1 = 0; b1 < n_items; b1 += T) {
+            const int i = b1 + tid;
+            int np = 0, lo3 = 0, tag = 0;
+            if (i < n_items) {
+                const int it = i >= n1_0;
+                const int k1 = i - (it ? n1_0 : 0);
+                const IterP& I = P.it[it];
+                const float x1 = X[szl[I.s1] + k1];
+                const float xc = I.scale3 * x1;
+                const int st3 = szl[I.s3], n3 = szl[I.s3 + 1] - st3;
+                lo3 = lower_bound_f(X + st3, n3, xc - I.dx3);
+                np = upper_bound_f(X + st3, n3, xc + I.dx3) - lo3;
+                tag = (it << 20) | k1;
+            }
+            ctr[0] += np;
+            int tot_p;
+            const int ps = block_exscan(np, tmp, tot_p);
+            sPS[tid] = ps;
+            sA[tid] = lo3;
+            sB[tid] = tag;
+            __syncthreads();
+            for (int pb = 0; pb < tot_p; pb += T) {
+                const int pidx = pb + tid;
+                int nt = 0, lo2 = 0, ptag = 0, k3 = 0;
+                if (pidx < tot_p) {
+                    const int o = owner_of(sPS, T, pidx);
+                    const int tg = sB[o];
+                    const int it = tg >> 20, k1 = tg & 0xFFFFF;
+                    k3 = sA[o] + (pidx - sPS[o]);
+                    const IterP& I = P.it[it];
+                    const float x1 = X[szl[I.s1] + k1], x3 = X[szl[I.s3] + k3];
+                    const float t13 = (x3 - x1) * I.inv_dz31;
+                    const float x0 = fmaf(-I.z1, t13, x1);
+                    const float ip = fmaf(P.invp_b * x0, x0, P.invp_a * fabsf(x0));
+                    if (ip > 0.f) {
+                        const float sg = x0 > 0.f ? 1.f : -1.f;
+                        const float ulo = fmaf(I.mlo_k, ip, -I.c0), uhi = fmaf(I.mhi_k, ip, I.c0);
+                        const float bs = fmaf(I.dz21, t13, x1);
+                        const float xa = fmaf(I.k3, -sg * ulo, bs), xb = fmaf(I.k3, -sg * uhi, bs);
+                        const int st2 = szl[I.s2], n2 = szl[I.s2 + 1] - st2;
+                        lo2 = lower_bound_f(X + st2, n2, fminf(xa, xb));
+                        nt = upper_bound_f(X + st2, n2, fmaxf(xa, xb)) - lo2;
+                    }
+                    ptag = tg;
+                }
+                ctr[1] += nt;
+                int tot_t;
+                const int ts = block_exscan(nt, tmp, tot_t);
+                sTS[tid] = ts;
+                sTA[tid] = lo2;
+                sTB[tid] = ptag;
+                sTC[tid] = k3;
+                __syncthreads();
+                for (int tb = 0; tb < tot_t; tb += T) {
+                    const int t = tb + tid;
+                    const int m = min(T, tot_t - tb);
+                    if (t < tot_t) {
+                        const int o = owner_of(sTS, T, t);
+                        const int tg = sTB[o];
+                        fifo[nfifo + (t - tb)] = pack_trip(tg >> 20, tg & 0xFFFFF, sTC[o], sTA[o] + (t - sTS[o]));
+                    }
+                    nfifo += m;
+                    __syncthreads();
+                    if (nfifo >= T) flush(T);
+                }
+                __syncthreads();
+            }
+            __syncthreads();
+        }
+        if (nfifo > 0) flush(nfifo);
+        if (tid == 0) ctr[3] += ncand;
+
+        if (ncand > CC) {
+            if (tid == 0) {
+                A.status[e] = -3;  // ST_OVERFLOW
+                A.item_count[item] = 0;
+            }
+            continue;
+        }
+        const int nc = ncand;
+
+        // ------------------------------------------------------------ clone kill
+        const int nxh = szl[6];
+        ull* tbl = nxh <= A.tbl_smem ? stab : g_tbl;
+        for (int i = tid; i < nxh; i += T) tbl[i] = ~0ull;
+        __syncthreads();
+        for (int k = tid; k < nc; k += T) {
+            const ull key = (ull(__float_as_uint(c_f[7 * CC + k])) << 32) | unsigned(k);
+#pragma unroll
+            for (int s = 0; s < 6; ++s) {
+                const int p = c_pos[s * CC + k];
+                if (p >= 0) atomicMin(&tbl[p], key);
+            }
+        }
+        __syncthreads();
+        int nk = 0;
+        for (int b = 0; b < nc; b += T) {
+            const int k = b + tid;
+            int keep = 0;
+            if (k < nc) {
+                const ull key = (ull(__float_as_uint(c_f[7 * CC + k])) << 32) | unsigned(k);
+                int owned = 0;
+#pragma unroll
+                for (int s = 0; s < 6; ++s) {
+                    const int p = c_pos[s * CC + k];
+                    owned += p >= 0 && tbl[p] == key;
+                }
+                keep = owned >= 3 || (owned >= 2 && c_nx[k] == 6);
+            }
+            int tot;
+            const int o = block_exscan(keep, tmp, tot);
+            if (keep) kept[nk + o] = k;
+            nk += tot;
+        }
+        if (tid == 0) ctr[4] += nk;
+        __syncthreads();
+
+        // ------------------------------------------------------------ UV
+        ull* ukey = nk <= A.key_smem ? skey : g_key;
+        for (int j = tid; j < nk; j += T) ukey[j] = ~0ull;
+        __syncthreads();
+        const int nuv = 2 * nk;
+        for (int b = 0; b < nuv; b += T) {
+            const int i = b + tid;
+            int cntc = 0, lo = 0;
+            if (i < nuv) {
+                const int k = kept[i >> 1], pass = i & 1;
+                const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
+                const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
+                const int ui = P.uv_init[pass];
+                const float Xi = x_at_uv(P, th, dth, ui);
+                const float t = P.ut[ui];
+                const float xa = fmaf(-P.uv_yhi[h], t, Xi), xb = fmaf(-P.uv_ylo[h], t, Xi);
+                const int st = szl[6 + ui], n = szl[7 + ui] - st;
+                lo = lower_bound_f(X + st, n, fminf(xa, xb));
+                cntc = upper_bound_f(X + st, n, fmaxf(xa, xb)) - lo;
+            }
+            ctr[5] += cntc;
+            int tot;
+            const int ps = block_exscan(cntc, tmp, tot);
+            sPS[tid] = ps;
+            sA[tid] = lo;
+            sB[tid] = i;
+            __syncthreads();
+            for (int cb = 0; cb < tot; cb += T) {
+                const int c = cb + tid;
+                if (c < tot) {
+                    const int o = owner_of(sPS, T, c);
+                    const int it2 = sB[o];
+                    const int j = it2 >> 1, pass = it2 & 1;
+                    const int kinit = sA[o] + (c - sPS[o]);
+                    const int k = kept[j];
+                    const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
+                    const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
+                    UV u;
+                    uv_combo(P, X, szl, th, dth, pass, kinit, true, u);
+                    if (u.n >= P.n_uv_min) {
+                        ++ctr[6];
+                        atomicMin(&ukey[j], uv_key(u.n, u.chi2, pass, kinit));
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        // ------------------------------------------------------------ seeds
+        int nseed = 0;
+        for (int b = 0; b < nk; b += T) {
+            const int j = b + tid;
+            const int has = j < nk && ukey[j] != ~0ull;
+            nseed += __syncthreads_count(has);
+        }
+        if (tid == 0) {
+            ull st = ~0ull;
+            if (nseed > 0) {
+                st = atomicAdd(A.pool_ctr, ull(nseed));
+                if (st + nseed > ull(A.pool_cap)) {
+                    A.status[e] = -3;
+                    st = ~0ull;
+                }
+            }
+            s_start = st;
+            A.item_start[item] = st == ~0ull ? 0 : static_cast<int32_t>(st);
+            A.item_count[item] = st == ~0ull ? 0 : nseed;
+            ctr[7] += st == ~0ull ? 0 : nseed;
+        }
+        __syncthreads();
+        if (s_start == ~0ull) continue;
+        int wbase = 0;
+        for (int b = 0; b < nk; b += T) {
+            const int j = b + tid;
+            const int has = j < nk && ukey[j] != ~0ull;
+            int tot;
+            const int o = block_exscan(has, tmp, tot);
+            if (has) {
+                const int64_t r = int64_t(s_start) + wbase + o;
+                const ull key = ukey[j];
+                const int pass = static_cast<int>((key >> 29) & 1);
+                const int kinit = static_cast<int>(key & ((1u << 29) - 1));
+                const int k = kept[j];
+                const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
+                const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
+                UV u;
+                uv_combo(P, X, szl, th, dth, pass, kinit, true, u);
+                int32_t* ho = A.pool_hits + r * 12;
+#pragma unroll
+                for (int s = 0; s < 6; ++s) {
+                    const int p = c_pos[s * CC + k];
+                    ho[kXLayer[s]] = p >= 0 ? A.corig[cbh + p] : -1;
+                    const int q = u.pos[s];
+                    ho[kULayer[s]] = q >= 0 ? A.corig[cbh + q] : -1;
+                }
+                const float a = th[0] + dth[0], bb = th[1] + dth[1], cc = th[2] + dth[2];
+                // y(z) = tyr z + wm + beta (z - zc - zm)
+                const float ty = u.tyr + u.beta;
+                const float y0 = fmaf(-u.beta, P.zc_uv + u.zm, u.wm);
+                const float yS = fmaf(u.tyr, P.zS, fmaf(u.beta, (P.zS - P.zc_uv) - u.zm, u.wm));
+                float* po = A.pool_params + r * 8;
+                po[0] = a; po[1] = bb; po[2] = cc; po[3] = c_f[6 * CC + k];
+                po[4] = y0; po[5] = ty; po[6] = u.chi2; po[7] = 0.f;
+                float* so = A.pool_state + r * 4;
+                so[0] = fmaf(th[2], P.fS, fmaf(th[1], P.zbS, th[0])) +
+                        fmaf(dth[2], P.fS, fmaf(dth[1], P.zbS, dth[0]));
+                so[1] = yS;
+                so[2] = fmaf(cc, P.dfS, bb);
+                so[3] = ty;
+                A.pool_n[r * 2] = static_cast<int8_t>(c_nx[k]);
+                A.pool_n[r * 2 + 1] = static_cast<int8_t>(u.n);
+            }
+            wbase += tot;
+        }
+    }
+    flush_counters(A.counters + C_PAIRS, ctr, 8);
+}
+
+// ===========================================================================
+// per-event CSR of the seed records
+// ===========================================================================
+
+__global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ GatherArgs A) {
+    __shared__ int tmp[36];
+    int64_t carry = 0;
+    for (int64_t b = 0; b < A.n_events; b += blockDim.x) {
+        const int64_t e = b + threadIdx.x;
+        const int c = e < A.n_events ? A.item_count[2 * e] + A.item_count[2 * e + 1] : 0;
+        int tot;
+        const int ex = block_exscan(c, tmp, tot);
+        if (e < A.n_events) A.ev_off[e] = static_cast<int32_t>(carry + ex);
+        carry += tot;
+    }
+    if (threadIdx.x == 0) A.ev_off[A.n_events] = static_cast<int32_t>(carry);
+}
+
+__global__ void __launch_bounds__(256) k_gather(const __grid_constant__ GatherArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); e < A.n_events; e += nw) {
+        const int c0 = A.item_count[2 * e], c1 = A.item_count[2 * e + 1];
+        const int s0 = A.item_start[2 * e], s1 = A.item_start[2 * e + 1];
+        const int64_t d0 = A.ev_off[e];
+        for (int k = lane; k < c0 + c1; k += 32) {
+            const int64_t src = k < c0 ? s0 + k : s1 + (k - c0);
+            const int64_t dst = d0 + k;
+#pragma unroll
+            for (int q = 0; q < 12; ++q) A.hits[dst * 12 + q] = A.pool_hits[src * 12 + q];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) A.params[dst * 8 + q] = A.pool_params[src * 8 + q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) A.state[dst * 4 + q] = A.pool_state[src * 4 + q];
+            A.n_hits[dst * 2] = A.pool_n[src * 2];
+            A.n_hits[dst * 2 + 1] = A.pool_n[src * 2 + 1];
+        }
+    }
+}
+
+// ===========================================================================
+// matching
+// ===========================================================================
+
+size_t match_smem_bytes(int velo_smem) { return sizeof(float) * 7 * size_t(velo_smem); }
+
+__global__ void __launch_bounds__(kMaxThreads)
+k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int VS = A.velo_smem, T = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5, nwarp = T >> 5;
+    float* vxh = reinterpret_cast<float*>(smem);
+    float* vxl = vxh + VS;
+    float* vyh = vxl + VS;
+    float* vyl = vyh + VS;
+    float* vtx = vyl + VS;
+    float* vty = vtx + VS;
+    float* vit = vty + VS;
+    __shared__ int s_item, s_cnt;
+    ull ctr[3] = {0, 0, 0};
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            s_item = atomicAdd(A.queue, 1);
+            s_cnt = 0;
+        }
+        __syncthreads();
+        const int64_t e = s_item;
+        if (e >= A.n_events) break;
+        const int64_t v0 = A.velo_off[e];
+        const int nv = static_cast<int>(A.velo_off[e + 1] - v0);
+        const int64_t s0 = A.seed_off[e];
+        const int ns = A.seed_off[e + 1] - static_cast<int>(s0);
+        for (int vc = 0; vc < nv; vc += VS) {
+            const int m = min(VS, nv - vc);
+            for (int v = tid; v < m; v += T) {
+                const float* st = A.velo + (v0 + vc + v) * 4;
+                const float x = st[0], y = st[1], tx = st[2], ty = st[3];
+                float p, pe, s, se;
+                two_prod(P.dAV_hi, tx, p, pe);
+                two_sum(x, p, s, se);
+                vxh[v] = s;
+                vxl[v] = se + fmaf(P.dAV_lo, tx, pe);
+                two_prod(P.dMV_hi, ty, p, pe);
+                two_sum(y, p, s, se);
+                vyh[v] = s;
+                vyl[v] = se + fmaf(P.dMV_lo, ty, pe);
+                vtx[v] = tx;
+                vty[v] = ty;
+                vit[v] = 1.f / fmaf(P.toly_b, fmaf(tx, tx, ty * ty), P.toly_a);
+            }
+            __syncthreads();
+            for (int s = wid; s < ns; s += nwarp) {
+                const float* st = A.seed_state + (s0 + s) * 4;
+                const float xS = st[0], yS = st[1], txS = st[2], tyS = st[3];
+                float p, pe, xh, xl, yh, yl;
+                two_prod(P.dAS_hi, txS, p, pe);
+                two_sum(xS, p, xh, xl);
+                xl += fmaf(P.dAS_lo, txS, pe);
+                two_prod(P.dMS_hi, tyS, p, pe);
+                two_sum(yS, p, yh, yl);
+                yl += fmaf(P.dMS_lo, tyS, pe);
+                const float dzx = P.Dx * fabsf(xS);
+                float best = FLT_MAX;
+                int bv = -1;
+                if (vc > 0) {
+                    bv = A.velo_idx[s0 + s];
+                    best = bv >= 0 ? A.chi2[s0 + s] : FLT_MAX;
+                }
+                int npre = 0;
+                for (int v = lane; v < m; v += 32) {
+                    const float dtx = vtx[v] - txS, dty = vty[v] - tyS;
+                    if (!(fabsf(dty) < P.cut_ty) || !(fabsf(dtx) < P.cut_tx)) continue;
+                    const float dy = (vyh[v] - yh) + (vyl[v] - yl);
+                    if (!(fabsf(dy) < P.cut_y)) continue;
+                    const float dz = fmaf(P.Bx, fabsf(dtx), fmaf(P.Cx, dtx * dtx, fmaf(P.Ex * vtx[v], vtx[v], dzx)));
+                    const float dx = fmaf(dz, dtx, (vxh[v] - xh) + (vxl[v] - xl));
+                    if (!(fabsf(dx) < P.cut_x)) continue;
+                    ++npre;
+                    const float tolx = fmaf(P.tolx_b, dtx * dtx, P.tolx_a);
+                    const float c2 = dx * dx / tolx + dy * dy * vit[v] + dtx * dtx * P.inv_toltx +
+                                     dty * dty * P.inv_tolty;
+                    const int vg = vc + v;
+                    if (c2 < P.chi2m_max && c2 < best) {
+                        best = c2;
+                        bv = vg;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    if (ob < best || (ob == best && ov >= 0 && (bv < 0 || ov < bv))) {
+                        best = ob;
+                        bv = ov;
+                    }
+                }
+                ctr[1] += npre;
+                if (lane == 0) {
+                    A.velo_idx[s0 + s] = bv;
+                    A.chi2[s0 + s] = bv >= 0 ? best : 0.f;
+                    ctr[0] += m;
+                }
+            }
+            __syncthreads();
+        }
+        if (nv == 0) {
+            for (int s = tid; s < ns; s += T) {
+                A.velo_idx[s0 + s] = -1;
+                A.chi2[s0 + s] = 0.f;
+            }
+        }
+        __syncthreads();
+        if (P.velo_unique) {
+            // a VELO segment keeps its best seed (lowest chi2, then lower seed
+            // index); losers are marked -2 - v so that concurrent readers still
+            // see which segment they held
+            for (int s = tid; s < ns; s += T) {
+                const int v = A.velo_idx[s0 + s];
+                if (v < 0) continue;
+                const float c = A.chi2[s0 + s];
+                for (int t = 0; t < ns; ++t) {
+                    if (t == s) continue;
+                    int vt = A.velo_idx[s0 + t];
+                    if (vt <= -2) vt = -2 - vt;
+                    if (vt != v) continue;
+                    const float ct = A.chi2[s0 + t];
+                    if (ct < c || (ct == c && t < s)) {
+                        A.velo_idx[s0 + s] = -2 - v;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int s = tid; s < ns; s += T) {
+                if (A.velo_idx[s0 + s] <= -2) {
+                    A.velo_idx[s0 + s] = -1;
+                    A.chi2[s0 + s] = 0.f;
+                }
+            }
+            __syncthreads();
+        }
+        int nl = 0;
+        for (int s = tid; s < ns; s += T) nl += A.velo_idx[s0 + s] >= 0;
+        nl = warp_sum(nl);
+        if (lane == 0 && nl) atomicAdd(&s_cnt, nl);
+        __syncthreads();
+        if (tid == 0) {
+            if (A.n_long) A.n_long[e] = s_cnt;
+            ctr[2] += s_cnt;
+        }
+    }
+    flush_counters(A.counters + C_MATCH_PAIRS, ctr, 3);
+}
+
+// ===========================================================================
+// launchers
+// ===========================================================================
+
+cudaError_t set_smem_limits(size_t build, size_t seed, size_t match) {
+    cudaError_t err;
+    if ((err = cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize, int(build))) != cudaSuccess)
+        return err;
+    if ((err = cudaFuncSetAttribute(k_seed, cudaFuncAttributeMaxDynamicSharedMemorySize, int(seed))) != cudaSuccess)
+        return err;
+    return cudaFuncSetAttribute(k_match, cudaFuncAttributeMaxDynamicSharedMemorySize, int(match));
+}
+
+int build_blocks_per_sm(int threads, size_t smem) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_build, threads, smem);
+    return n;
+}
+int seed_blocks_per_sm(int threads, size_t smem) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed, threads, smem);
+    return n;
+}
+int match_blocks_per_sm(int threads, size_t smem) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_match, threads, smem);
+    return n;
+}
+
+cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int threads, cudaStream_t s) {
+    k_build<<<grid, threads, build_smem_bytes(a.bins, a.smem_hits), s>>>(P, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s) {
+    k_seed<<<grid, threads, seed_smem_bytes(threads, a.smem_hits, a.tbl_smem, a.key_smem), s>>>(P, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
+    k_scan<<<1, 1024, 0, s>>>(a);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const int64_t warps = a.n_events;
+    const int grid = static_cast<int>(std::min<int64_t>((warps + 7) / 8, 4096));
+    if (grid > 0) k_gather<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_match(const DevParams& P, const MatchArgs& a, int grid, int threads, cudaStream_t s) {
+    k_match<<<grid, threads, match_smem_bytes(a.velo_smem), s>>>(P, a);
+    return cudaGetLastError();
+}
+
+}  // namespace st

@@ -1,0 +1,112 @@
+// st_kernels.cuh -- launch interface between the host runtime and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "st_device.cuh"
+
+namespace st {
+
+// counters (same order as st_counters)
+enum {
+    C_PAIRS = 0, C_TRIPLETS, C_EXT_OK, C_CANDS, C_KEPT, C_UV_INIT, C_UV_CANDS, C_SEEDS,
+    C_MATCH_PAIRS, C_MATCH_PRESEL, C_MATCHED, C_HITS, C_EVENTS, C_N
+};
+
+struct BuildArgs {
+    int64_t n_events;
+    const int64_t* ev_off;
+    const float* x;
+    const int32_t* zone;
+    const float* z;       // may be null
+    const float* dxdy;    // may be null
+    int32_t max_hits;
+    int32_t bins;         // buckets per container slot (power of two)
+    int32_t smem_hits;    // per-hit arrays in shared memory up to this many hits
+    int64_t cont_cap;     // entries of cx / corig
+    float* cx;            // container x
+    int32_t* corig;       // container: event-local hit index
+    int32_t* zoff;        // [n_events * 25]
+    int32_t* status;      // [n_events]
+    uint8_t* big;         // per-CTA per-hit arrays for larger events
+    int64_t big_stride;   // bytes per CTA
+    int32_t* queue;
+    unsigned long long* counters;
+};
+
+struct SeedArgs {
+    int64_t n_events;
+    const int64_t* ev_off;
+    const float* cx;
+    const int32_t* corig;
+    const int32_t* zoff;
+    int32_t* status;
+    int32_t smem_hits;    // hits of a half staged in shared memory up to this
+    int32_t cand_cap;     // candidates per work item
+    int32_t tbl_smem;     // clone table entries in shared memory
+    int32_t key_smem;     // UV keys in shared memory
+    uint8_t* slot;        // per-CTA scratch
+    int64_t slot_stride;  // bytes per CTA
+    int32_t max_xhits;    // size of the per-CTA clone table in scratch
+    // staging pool of seed records
+    int32_t* pool_hits;
+    float* pool_params;
+    float* pool_state;
+    int8_t* pool_n;
+    int64_t pool_cap;
+    unsigned long long* pool_ctr;
+    int32_t* item_start;
+    int32_t* item_count;
+    int32_t* queue;
+    unsigned long long* counters;
+};
+
+struct GatherArgs {
+    int64_t n_events;
+    const int32_t* item_start;
+    const int32_t* item_count;
+    const int32_t* pool_hits;
+    const float* pool_params;
+    const float* pool_state;
+    const int8_t* pool_n;
+    int64_t cap;
+    int32_t* ev_off;
+    int32_t* hits;
+    float* params;
+    float* state;
+    int8_t* n_hits;
+    int32_t* status;
+};
+
+struct MatchArgs {
+    int64_t n_events;
+    const int64_t* velo_off;
+    const float* velo;
+    const int32_t* seed_off;
+    const float* seed_state;
+    int32_t* velo_idx;
+    float* chi2;
+    int32_t* n_long;
+    int32_t velo_smem;    // VELO segments per shared-memory chunk
+    int32_t* queue;
+    unsigned long long* counters;
+};
+
+size_t build_smem_bytes(int bins, int smem_hits);
+size_t seed_smem_bytes(int threads, int smem_hits, int tbl_smem, int key_smem);
+size_t seed_slot_bytes(int cand_cap, int max_xhits);
+size_t match_smem_bytes(int velo_smem);
+
+cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int threads, cudaStream_t s);
+cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s);
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
+cudaError_t launch_match(const DevParams& P, const MatchArgs& a, int grid, int threads, cudaStream_t s);
+
+// occupancy helpers
+int build_blocks_per_sm(int threads, size_t smem);
+int seed_blocks_per_sm(int threads, size_t smem);
+int match_blocks_per_sm(int threads, size_t smem);
+cudaError_t set_smem_limits(size_t build, size_t seed, size_t match);
+
+}  // namespace st

@@ -1,0 +1,168 @@
+"""GPU-vs-oracle comparison harness used by the GPU tests and the smoke check.
+
+Acceptance rules (per event, seeds compared as their 12-entry hit lists of
+event-local hit indices):
+  * agreement: |GPU set & oracle set| / |GPU set | oracle set| over the batch
+    must be at least AGREE_MIN (99.9%);
+  * every seed in only one of the two sets must be traced to an oracle ledger
+    decision whose margin is at most TAU (1e-5, relative to the magnitude of
+    the numbers that decision is made from): the seed shares a hit with that
+    decision, or with an oracle x-z candidate that does;
+  * for seeds in both sets the fitted quantities must agree within the
+    tolerances of TOL (positions 1e-3 mm, slopes 1e-6; derived ones below).
+Matching is compared on identical seed states (the GPU's float32 states are
+the input of both sides): the chosen VELO index per seed must be equal unless
+a matching ledger entry of that seed is within TAU.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Dict, List
+
+import numpy as np
+
+import oracle
+
+TAU = 1e-5
+AGREE_MIN = 0.999
+# |f(zb)| over the SciFi is below 1e6 mm^2, so a curvature difference dc moves
+# positions by at most 1e6 * dc: 1e-3 mm <=> dc <= 1e-9 / mm.
+# y0 is y extrapolated from z ~ 8.6 m to z = 0: 1e-3 mm + 1e4 mm * 1e-6.
+TOL = {"a": 1e-3, "b": 1e-6, "c": 1e-9, "y0": 1.1e-2, "ty": 1e-6,
+       "x_s": 1e-3, "y_s": 1e-3, "tx_s": 1e-6, "ty_s": 1e-6}
+CHI2_REL = 1e-4
+
+
+def config_pair(zmx=None, **overrides):
+    """The oracle's and the CUDA library's configurations with the same
+    overrides (each side starts from its own defaults)."""
+    from paper_2606_14480_gb300 import st
+    ov = dict(overrides)
+    if zmx is not None:
+        ov["zmx"] = np.asarray(zmx, dtype=np.float64)
+    tuning = {k: ov.pop(k) for k in list(ov) if k in ("threads_seed", "threads_build", "threads_match",
+                                                        "ctas_per_sm", "smem_hits", "cand_cap")}
+    ocfg = oracle.default_config(**ov)
+    gcfg = st.st_config_default(**ov, **tuning)
+    return ocfg, gcfg
+
+
+@dataclass
+class Report:
+    n_gpu: int = 0
+    n_cpu: int = 0
+    n_common: int = 0
+    untraced: List[tuple] = field(default_factory=list)
+    traced: int = 0
+    max_err: Dict[str, float] = field(default_factory=dict)
+    bad_params: List[tuple] = field(default_factory=list)
+    chi2_rel: float = 0.0
+
+    @property
+    def agreement(self):
+        u = self.n_gpu + self.n_cpu - self.n_common
+        return 1.0 if u == 0 else self.n_common / u
+
+    def merge(self, o: "Report"):
+        self.n_gpu += o.n_gpu
+        self.n_cpu += o.n_cpu
+        self.n_common += o.n_common
+        self.untraced += o.untraced
+        self.traced += o.traced
+        self.bad_params += o.bad_params
+        for k, v in o.max_err.items():
+            self.max_err[k] = max(self.max_err.get(k, 0.0), v)
+        self.chi2_rel = max(self.chi2_rel, o.chi2_rel)
+
+    def summary(self):
+        return (f"gpu={self.n_gpu} cpu={self.n_cpu} common={self.n_common} agree={self.agreement:.6f} "
+                f"traced={self.traced} untraced={len(self.untraced)} bad_params={len(self.bad_params)} "
+                f"chi2_rel={self.chi2_rel:.2e} max_err={ {k: float(f'{v:.3g}') for k, v in self.max_err.items()} }")
+
+
+def compare_seeding_event(e, gpu: Dict[str, np.ndarray], ref: Dict[str, object], tau=TAU) -> Report:
+    s0, s1 = int(gpu["ev_off"][e]), int(gpu["ev_off"][e + 1])
+    gh = gpu["hits"][s0:s1]
+    G = {tuple(int(v) for v in h): s0 + i for i, h in enumerate(gh)}
+    seeds = ref["seeds"]
+    O = {tuple(int(v) for v in s["hits"]): i for i, s in enumerate(seeds)}
+    r = Report(n_gpu=len(G), n_cpu=len(O))
+    common = G.keys() & O.keys()
+    r.n_common = len(common)
+    diff = G.keys() ^ O.keys()
+    if diff:
+        led = ref["ledger"]
+        near = led[led["margin"] <= tau]
+        near_hits = set(int(h) for h in near["hits"].ravel() if h >= 0)
+        ext = set(near_hits)
+        for c in ref.get("cands", []):
+            hs = {int(h) for h in c["hits"] if h >= 0}
+            if hs & near_hits:
+                ext |= hs
+        for t in diff:
+            if {h for h in t if h >= 0} & ext:
+                r.traced += 1
+            else:
+                r.untraced.append((e, t, "gpu" if t in G else "oracle"))
+    for t in common:
+        gi, oi = G[t], O[t]
+        s = seeds[oi]
+        p = gpu["params"][gi]
+        q = gpu["state"][gi]
+        vals = {"a": (p[0], s["a"]), "b": (p[1], s["b"]), "c": (p[2], s["c"]), "y0": (p[4], s["y0"]),
+                "ty": (p[5], s["ty"]), "x_s": (q[0], s["x_s"]), "y_s": (q[1], s["y_s"]),
+                "tx_s": (q[2], s["tx_s"]), "ty_s": (q[3], s["ty_s"])}
+        for k, (g, o) in vals.items():
+            d = abs(float(g) - float(o))
+            r.max_err[k] = max(r.max_err.get(k, 0.0), d)
+            if d > TOL[k]:
+                r.bad_params.append((e, t, k, float(g), float(o)))
+        for gi_, ok in ((3, "chi2x"), (6, "chi2y")):
+            g, o = float(p[gi_]), float(s[ok])
+            rel = abs(g - o) / max(abs(o), 1e-3)
+            r.chi2_rel = max(r.chi2_rel, rel)
+        if int(gpu["n_hits"][gi][0]) != int(s["nx"]) or int(gpu["n_hits"][gi][1]) != int(s["nuv"]):
+            r.bad_params.append((e, t, "n_hits", tuple(gpu["n_hits"][gi]), (s["nx"], s["nuv"])))
+    return r
+
+
+def oracle_seeding(ocfg, batch, events, tau_record=1e-4, threads=None):
+    return oracle.seeding_batch(ocfg, batch, events, threads=threads, cands=True, ledger_tau=tau_record)
+
+
+def compare_seeding(gpu, ocfg, batch, events=None, tau=TAU) -> Report:
+    events = list(range(batch.n_events)) if events is None else list(events)
+    refs = oracle_seeding(ocfg, batch, events)
+    rep = Report()
+    for e, ref in zip(events, refs):
+        assert ref["status"] == 0
+        rep.merge(compare_seeding_event(e, gpu, ref, tau))
+    return rep
+
+
+def compare_matching(gpu, ocfg, batch, events=None, tau=TAU):
+    """Matching on the GPU's own seed states: returns (n_seeds, mismatches
+    untraced, traced, max relative chi2 difference)."""
+    events = list(range(batch.n_events)) if events is None else list(events)
+    n = traced = 0
+    untraced = []
+    chi_rel = 0.0
+    for e in events:
+        s0, s1 = int(gpu["ev_off"][e]), int(gpu["ev_off"][e + 1])
+        m = oracle.matching_event(ocfg, batch.velo_of(e), gpu["state"][s0:s1], ledger_tau=1e-4)
+        gv = gpu["velo_idx"][s0:s1]
+        n += s1 - s0
+        led = m["ledger"]
+        near = set(int(s) for s in led[led["margin"] <= tau]["hits"][:, 0]) if len(led) else set()
+        for k in np.nonzero(gv != m["velo_idx"])[0]:
+            if k in near:
+                traced += 1
+            else:
+                untraced.append((e, int(k), int(gv[k]), int(m["velo_idx"][k])))
+        both = (gv >= 0) & (gv == m["velo_idx"])
+        if both.any():
+            g = gpu["chi2"][s0:s1][both].astype(np.float64)
+            o = m["chi2"][both]
+            chi_rel = max(chi_rel, float(np.max(np.abs(g - o) / np.maximum(o, 1e-6))))
+    return n, untraced, traced, chi_rel
