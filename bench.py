@@ -224,6 +224,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--serve-events", type=int, default=400000, help="bound on served events per rate")
     ap.add_argument("--serve-rates", default="0.5", help="offered rates as fractions of batched capacity")
     ap.add_argument("--per-event", type=int, default=200, help="events timed with per-event launches")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -285,6 +286,7 @@ def main():
         clk = clocks.stop()
     counters = ctx.st_read_counters(reset=True)
     total_ms = float(np.sum(step_ms))
+    log(f"batched: {np.mean(step_ms):.3f} ms/step, kernels {kms}")
     if ws > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -339,18 +341,21 @@ def main():
     # ---------------- e2e through the public host API (pipeline)
     ctx2 = st.Context(cfg, device=local)
     ctx2.st_pipeline_configure(n_slots=2, max_events_per_slot=n_ev, max_hits_per_slot=batch.n_hits + 16,
-                               max_hits_per_event=db.max_hits, max_velo_per_event=1024)
+                               max_hits_per_event=db.max_hits, max_velo_per_event=1024,
+                               max_velo_per_slot=int(batch.velo.shape[0]) + 16)
     hh, hv, keep = st.HostBuffers.inputs(batch.ev_off, batch.x, batch.zone, batch.velo_off, batch.velo)
     hb = st.HostBuffers(n_ev, cap)
     for _ in range(2):
         t = ctx2.pipeline_submit(hh, hv)
-        ctx2.pipeline_poll(t, hb.seeds, hb.long, -1)
+        rc, _ = ctx2.pipeline_poll(t, hb.seeds, hb.long, 60_000_000)
+        assert rc == st.ST_OK, rc
     h2d = 8 * (n_ev + 1) * 2 + 8 * batch.n_hits + 16 * batch.velo.shape[0]
     e2e_t = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
         t = ctx2.pipeline_submit(hh, hv)
-        rc, info = ctx2.pipeline_poll(t, hb.seeds, hb.long, -1)
+        rc, info = ctx2.pipeline_poll(t, hb.seeds, hb.long, 60_000_000)
+        assert rc == st.ST_OK, rc
         e2e_t.append(time.perf_counter() - t0)
     ns = int(hb.ev_off[-1])
     d2h = 4 * (n_ev + 1) + 8 * n_ev + ns * (48 + 32 + 16 + 2 + 8)
@@ -359,6 +364,7 @@ def main():
         t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_total = float(t.item())
+    log(f"e2e: {1000 * e2e_total / args.steps:.3f} ms/step")
     result["e2e"] = {"value": ws * n_ev * args.steps / e2e_total, "unit": "events/s",
                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                      "api": "pipeline_submit + pipeline_poll, host buffers, one batch in flight"}
@@ -396,9 +402,11 @@ def main():
                                "mode": "seeding_run + matching_run per event, one stream"}
         del C
         ctx3.close()
+        log(f"per-event: {pe_ms / pe:.4f} ms/event")
 
         # ---------------- served: continuous batching of a Poisson request stream
         result["served"] = serve(st, cfg, value, args, local)
+        log(f"served: {result['served']}")
 
         # ---------------- CPU baseline: the oracle on the host cores
         if not args.no_cpu_baseline:
@@ -416,40 +424,68 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+def poll_grow(st, ctx, ticket, n_events, timeout_us=60_000_000):
+    """pipeline_poll into host buffers, growing them while the library
+    reports ST_OVERFLOW (the ticket is kept in that case)."""
+    cap = n_events * 300 + 1024
+    while True:
+        hb = st.HostBuffers(n_events, cap)
+        try:
+            rc, info = ctx.pipeline_poll(ticket, hb.seeds, hb.long, timeout_us)
+        except st.StError as exc:
+            if exc.code == st.ST_OVERFLOW:
+                cap *= 2
+                continue
+            raise
+        if rc != st.ST_OK:
+            raise RuntimeError(f"pipeline_poll: {st.STATUS_NAMES.get(rc, rc)}")
+        return info
+
+
 def serve(st, cfg, batched_rate, args, local):
-    """Poisson arrivals of request batches (sizes log-uniform 1-4096, events
-    from a pool with log-normal occupancy) at fractions of the batched rate."""
+    """Poisson arrivals of request batches (sizes log-uniform 1-4096; events
+    are contiguous windows of a pool with log-normal occupancy, passed to
+    pipeline_submit without a copy) at fractions of the batched rate."""
     from synth import make_workload
     from synth.events import poisson_arrivals, serving_requests
-    pool = make_workload("uneven", n_events=4096, seed=1005)
+    pool = make_workload("uneven", n_events=8192, seed=1005)
+    ev_off = np.ascontiguousarray(pool.ev_off, np.int64)
+    velo_off = np.ascontiguousarray(pool.velo_off, np.int64)
+    x = np.ascontiguousarray(pool.x, np.float32)
+    zone = np.ascontiguousarray(pool.zone, np.int32)
+    velo = np.ascontiguousarray(pool.velo, np.float32)
     ctx = st.Context(cfg, device=local)
-    ctx.st_pipeline_configure(n_slots=4, max_events_per_slot=4096, max_hits_per_slot=int(pool.n_hits) + 16,
-                              max_hits_per_event=int(np.max(np.diff(pool.ev_off))), max_velo_per_event=4096)
+    mh = int(np.max(np.diff(ev_off)))
+    ctx.st_pipeline_configure(n_slots=4, max_events_per_slot=4096, max_hits_per_slot=4096 * 4000,
+                              max_hits_per_event=mh, max_velo_per_event=4096, max_velo_per_slot=4096 * 1024)
     out = {}
-    for frac in [float(f) for f in args.serve_rates.split(",")]:
+    rng = np.random.default_rng(1007)
+    for frac in [float(f) for f in args.serve_rates.split(",") if f]:
         rate = frac * batched_rate  # events/s offered
-        sizes = serving_requests(int(rate * args.serve_seconds) + 1, seed=1005)
+        n_events_total = int(min(rate * args.serve_seconds, args.serve_events))
+        sizes = serving_requests(max(1, n_events_total), seed=1005)
         n_req = len(sizes)
-        mean = float(np.mean(sizes))
-        arr = poisson_arrivals(n_req, rate / mean, seed=1006)
-        starts = np.cumsum(np.concatenate([[0], sizes[:-1]])) % pool.n_events
-        reqs = []
-        for s0, n in zip(starts, sizes):
-            idx = (np.arange(n) + s0) % pool.n_events
-            sub = pool.subset(idx)
-            reqs.append(st.HostBuffers.inputs(sub.ev_off, sub.x, sub.zone, sub.velo_off, sub.velo))
+        arr = poisson_arrivals(n_req, rate / float(np.mean(sizes)), seed=1006)
+        starts = [int(rng.integers(0, pool.n_events - n + 1)) for n in sizes]
         lat = [None] * n_req
         tickets = [None] * n_req
         done = threading.Event()
 
+        errors = []
+
         def poller():
-            for i in range(n_req):
-                while tickets[i] is None:
-                    time.sleep(0.0002)
-                hb = st.HostBuffers(int(sizes[i]), int(sizes[i]) * 300 + 64)
-                rc, info = ctx.pipeline_poll(tickets[i], hb.seeds, hb.long, -1)
-                lat[i] = (info.t_done_ns - info.t_submit_ns) / 1e6
-            done.set()
+            try:
+                for i in range(n_req):
+                    while tickets[i] is None:
+                        if errors:
+                            return
+                        time.sleep(0.0002)
+                    info = poll_grow(st, ctx, tickets[i], int(sizes[i]))
+                    lat[i] = (info.t_done_ns - info.t_submit_ns) / 1e6
+            except Exception as exc:  # surfaced by the main thread
+                errors.append(exc)
+            finally:
+                done.set()
 
         th = threading.Thread(target=poller, daemon=True)
         th.start()
@@ -458,13 +494,22 @@ def serve(st, cfg, batched_rate, args, local):
             wait = arr[i] - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(wait)
-            hits, velo, keep = reqs[i]
-            tickets[i] = ctx.pipeline_submit(hits, velo)
-        done.wait()
+            s0, n = starts[i], int(sizes[i])
+            hits = st.StHits(n, ev_off[s0:].ctypes.data, x.ctypes.data, zone.ctypes.data, None, None, mh, 0)
+            vel = st.StVelo(n, velo_off[s0:].ctypes.data, velo.ctypes.data)
+            try:
+                tickets[i] = ctx.pipeline_submit(hits, vel)
+            except Exception as exc:
+                errors.append(exc)
+                break
+        if not done.wait(timeout=120.0 + 20.0 * args.serve_seconds):
+            raise RuntimeError("served requests did not complete in time")
+        if errors:
+            raise errors[0]
         wall = time.perf_counter() - t0
         lat_a = np.array(lat)
         out[f"{frac:g}"] = {"offered_events_per_s": rate, "events_per_s": float(np.sum(sizes) / wall),
-                            "requests": n_req, "events": int(np.sum(sizes)),
+                            "requests": n_req, "events": int(np.sum(sizes)), "wall_s": wall,
                             "p50_ms": float(np.percentile(lat_a, 50)), "p99_ms": float(np.percentile(lat_a, 99))}
     ctx.close()
     return out

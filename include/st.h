@@ -247,6 +247,7 @@ typedef struct {
     int32_t max_hits_per_event;
     int32_t max_velo_per_event;
     int64_t mem_cap_bytes;       /* device + pinned memory the pipeline may hold */
+    int64_t max_velo_per_slot;   /* VELO segments packed into one launch */
 } st_pipeline_config;
 
 void st_pipeline_config_default(st_pipeline_config* pc);

@@ -393,7 +393,9 @@ static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 // kernel timing marks on the launch stream (only for the context's own workspace)
 static void tmark(st_ctx* ctx, const Workspace& w, int k, int end, cudaStream_t s) {
     if (!ctx->timing || &w != &ctx->ws) return;
-    cudaEventRecord(ctx->tev[k][end], s);
+    // external: inside a stream capture the record becomes a graph node that
+    // records the event on every launch of the graph
+    cudaEventRecordWithFlags(ctx->tev[k][end], s, cudaEventRecordExternal);
     ctx->tused[k] = true;
 }
 
@@ -883,13 +885,14 @@ extern "C" void st_pipeline_config_default(st_pipeline_config* pc) {
     pc->max_hits_per_event = 16384;
     pc->max_velo_per_event = 2048;
     pc->mem_cap_bytes = 40ll << 30;
+    pc->max_velo_per_slot = 1ll << 20;
 }
 
 static size_t slot_device_bytes(st_ctx* ctx, const st_pipeline_config& pc, int64_t seeds_cap) {
     Workspace t;
     size_t b = carve(ctx, t, pc.max_events_per_slot, pc.max_hits_per_slot, pc.max_hits_per_event, seeds_cap, nullptr);
     const int64_t E = pc.max_events_per_slot, Hh = pc.max_hits_per_slot;
-    const int64_t Vv = int64_t(pc.max_events_per_slot) * 64;
+    const int64_t Vv = pc.max_velo_per_slot;
     b += 2 * 8 * size_t(E + 1) + 8 * size_t(Hh) + 16 * size_t(Vv);
     b += size_t(seeds_cap) * (48 + 32 + 16 + 2 + 8) + 12 * size_t(E + 1);
     return b;
@@ -898,7 +901,7 @@ static size_t slot_device_bytes(st_ctx* ctx, const st_pipeline_config& pc, int64
 static int slot_alloc(st_ctx* ctx, Slot& S, const st_pipeline_config& pc) {
     S.cap_events = pc.max_events_per_slot;
     S.cap_hits = pc.max_hits_per_slot;
-    S.cap_velo = int64_t(pc.max_events_per_slot) * 64;
+    S.cap_velo = pc.max_velo_per_slot;
     S.cap_seeds = std::max<int64_t>(1024, S.cap_hits / 8);
     ST_CUDA(ctx, cudaStreamCreateWithFlags(&S.stream, cudaStreamNonBlocking));
     ST_CUDA(ctx, cudaEventCreateWithFlags(&S.ev_counts, cudaEventDisableTiming));
@@ -1119,12 +1122,14 @@ static int pipeline_configure_locked(st_ctx* ctx, const st_pipeline_config* pcin
     if (ctx->pipe) return set_err(ctx, ST_ESTATE, "pipeline already configured");
     st_pipeline_config pc = *pcin;
     if (pc.n_slots < 1 || pc.max_events_per_slot < 1 || pc.max_hits_per_slot < 1 || pc.max_hits_per_event < 1 ||
-        pc.max_hits_per_event > 65535 || pc.max_velo_per_event < 1 || pc.mem_cap_bytes <= 0)
+        pc.max_hits_per_event > 65535 || pc.max_velo_per_event < 1 || pc.mem_cap_bytes <= 0 ||
+        pc.max_velo_per_slot < 1)
         return set_err(ctx, ST_EINVAL, "bad pipeline config");
     ST_CUDA(ctx, cudaSetDevice(ctx->device));
     const int64_t seeds_cap = std::max<int64_t>(1024, pc.max_hits_per_slot / 8);
-    const size_t per_slot = slot_device_bytes(ctx, pc, seeds_cap) +
-                            size_t(pc.max_hits_per_slot) * 8 + size_t(pc.max_events_per_slot) * 64 * 16;
+    // device buffers and workspace, plus the pinned staging of the same size
+    const size_t per_slot = slot_device_bytes(ctx, pc, seeds_cap) + size_t(pc.max_hits_per_slot) * 8 +
+                            size_t(pc.max_velo_per_slot) * 16 + size_t(seeds_cap) * 110;
     const int64_t fit = pc.mem_cap_bytes / int64_t(per_slot);
     if (fit < 1) return set_err(ctx, ST_ENOMEM, "one pipeline slot (%zu bytes) exceeds mem_cap_bytes", per_slot);
     pc.n_slots = static_cast<int32_t>(std::min<int64_t>(pc.n_slots, fit));

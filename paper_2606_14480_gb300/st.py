@@ -71,7 +71,8 @@ class StCounters(C.Structure):
 class StPipelineConfig(C.Structure):
     _fields_ = [("n_slots", C.c_int32), ("max_events_per_slot", C.c_int32),
                 ("max_hits_per_slot", C.c_int64), ("max_hits_per_event", C.c_int32),
-                ("max_velo_per_event", C.c_int32), ("mem_cap_bytes", C.c_int64)]
+                ("max_velo_per_event", C.c_int32), ("mem_cap_bytes", C.c_int64),
+                ("max_velo_per_slot", C.c_int64)]
 
 
 class StRequestInfo(C.Structure):

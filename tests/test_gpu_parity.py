@@ -294,7 +294,7 @@ def test_pipeline_alone_and_in_the_mix(zmx):
         out = st.run_batch(ctx, st.DeviceBatch.from_synth(sub, max_hits=8000))
         torch.cuda.synchronize()
         alone.append(out.to_numpy())
-    ctx.st_pipeline_configure(n_slots=3, max_events_per_slot=128, max_hits_per_slot=128 * 4000,
+    ctx.st_pipeline_configure(n_slots=3, max_events_per_slot=256, max_hits_per_slot=256 * 4000,
                               max_hits_per_event=8000, max_velo_per_event=1024)
     tickets, keep = [], []
     for a, c in zip(cuts[:-1], cuts[1:]):
