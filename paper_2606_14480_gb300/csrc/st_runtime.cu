@@ -523,7 +523,9 @@ extern "C" int st_create(const st_config* cfg, int device, st_ctx** out) {
         delete ctx;
         return ST_EINVAL;
     }
-    e = set_smem_limits(ctx->build_smem_max, ctx->seed_smem, ctx->match_smem);
+    // a permission ceiling, not a reservation: set it to the device maximum so
+    // that contexts with different configurations never lower each other's
+    e = set_smem_limits(ctx->smem_optin, ctx->smem_optin, ctx->smem_optin);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->counters, sizeof(unsigned long long) * C_N);
     if (e == cudaSuccess) e = cudaMemset(ctx->counters, 0, sizeof(unsigned long long) * C_N);
     if (e != cudaSuccess) {
