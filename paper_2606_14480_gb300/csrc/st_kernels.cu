@@ -924,13 +924,20 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
 // launchers
 // ===========================================================================
 
-cudaError_t set_smem_limits(size_t build, size_t seed, size_t match) {
-    cudaError_t err;
-    if ((err = cudaFuncSetAttribute(k_build, cudaFuncAttributeMaxDynamicSharedMemorySize, int(build))) != cudaSuccess)
-        return err;
-    if ((err = cudaFuncSetAttribute(k_seed, cudaFuncAttributeMaxDynamicSharedMemorySize, int(seed))) != cudaSuccess)
-        return err;
-    return cudaFuncSetAttribute(k_match, cudaFuncAttributeMaxDynamicSharedMemorySize, int(match));
+// Raise each kernel's dynamic shared-memory ceiling to what the device allows
+// next to the kernel's own static shared memory (opt-in maximum - static).
+cudaError_t set_smem_limits(size_t optin) {
+    const void* fns[] = {reinterpret_cast<const void*>(k_build), reinterpret_cast<const void*>(k_seed),
+                         reinterpret_cast<const void*>(k_match)};
+    for (const void* f : fns) {
+        cudaFuncAttributes fa;
+        cudaError_t err = cudaFuncGetAttributes(&fa, f);
+        if (err != cudaSuccess) return err;
+        const int dyn = static_cast<int>(optin) - static_cast<int>(fa.sharedSizeBytes);
+        if ((err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess)
+            return err;
+    }
+    return cudaSuccess;
 }
 
 int build_blocks_per_sm(int threads, size_t smem) {

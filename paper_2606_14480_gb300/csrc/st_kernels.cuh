@@ -107,6 +107,6 @@ cudaError_t launch_match(const DevParams& P, const MatchArgs& a, int grid, int t
 int build_blocks_per_sm(int threads, size_t smem);
 int seed_blocks_per_sm(int threads, size_t smem);
 int match_blocks_per_sm(int threads, size_t smem);
-cudaError_t set_smem_limits(size_t build, size_t seed, size_t match);
+cudaError_t set_smem_limits(size_t optin);
 
 }  // namespace st

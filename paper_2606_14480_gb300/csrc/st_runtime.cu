@@ -519,13 +519,13 @@ extern "C" int st_create(const st_config* cfg, int device, st_ctx** out) {
     ctx->seed_smem = seed_smem_bytes(c.threads_seed, c.smem_hits, ctx->tbl_smem, ctx->key_smem);
     ctx->match_smem = match_smem_bytes(ctx->velo_smem);
     ctx->build_smem_max = build_smem_bytes(512, kBuildSmemHits);
-    if (ctx->seed_smem > ctx->smem_optin || ctx->build_smem_max > ctx->smem_optin) {
+    if (ctx->seed_smem + 64 > ctx->smem_optin || ctx->build_smem_max + 64 > ctx->smem_optin) {
         delete ctx;
         return ST_EINVAL;
     }
     // a permission ceiling, not a reservation: set it to the device maximum so
     // that contexts with different configurations never lower each other's
-    e = set_smem_limits(ctx->smem_optin, ctx->smem_optin, ctx->smem_optin);
+    e = set_smem_limits(ctx->smem_optin);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->counters, sizeof(unsigned long long) * C_N);
     if (e == cudaSuccess) e = cudaMemset(ctx->counters, 0, sizeof(unsigned long long) * C_N);
     if (e != cudaSuccess) {
