@@ -236,6 +236,43 @@ int st_kernel_ms(st_ctx* ctx, float ms[4]);
 int st_read_counters(st_ctx* ctx, st_counters* out, int reset);
 
 /* ---------------------------------------------------------------------- */
+/* Seeding without allocation.  The paper has no counterpart to this entry   */
+/* point; it exists for callers that cannot allocate device memory.          */
+/* ---------------------------------------------------------------------- */
+
+/* Size of the scratch array compiled into the library: every GPU that loads
+ * libst holds this much device memory until the process exits. */
+#define ST_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* seeding_run without a context and without any allocation: the same
+ * kernels, with all intermediate data (hit containers, per-event slot
+ * offsets, work queues, per-CTA candidate storage, seed pool) in one fixed
+ * array of ST_STATIC_SCRATCH_BYTES inside the library.  For callers that
+ * cannot call cudaMalloc: a process whose device memory belongs to a host
+ * framework's own allocator, or a real-time event loop that forbids
+ * allocation after start-up because cudaMalloc / cudaFree can synchronise the
+ * device and stall it.
+ *
+ * Arguments and output are those of seeding_run (DEVICE pointers owned by the
+ * caller), cfg replaces the context, and the work runs on the device that is
+ * current for the calling thread.  The results equal seeding_run's.
+ * Limits: max_hits_per_event <= 6144, and the batch must fit the array:
+ * about 8*n_events*max_hits_per_event + 98*seeds->cap bytes plus one
+ * candidate store of 64*cand_cap + 8*(max_hits_per_event + cand_cap) bytes
+ * (e.g. 128 events of up to 4096 hits with 40 000 seeds fit); otherwise it
+ * returns ST_OVERFLOW and writes nothing.  A NUL-terminated message goes to
+ * err (may be NULL) on every failure.
+ *
+ * The first call on a device sets that device up (looks up the array's device
+ * address and raises the kernels' shared-memory limits); make that first call
+ * before any stream capture.  Every call reuses the same array: work queues
+ * and counters are cleared at the start of each call, and calls that overlap
+ * on the GPU (different streams or host threads at once) race on it, so
+ * serialise them.  Returns ST_OK, ST_EINVAL, ST_OVERFLOW or ST_ECUDA. */
+int seeding_run_static(const st_config* cfg, const st_hits* hits, st_seeds* seeds, void* cuda_stream,
+                       char* err, int32_t err_len);
+
+/* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of host-side event batches.                */
 /* ---------------------------------------------------------------------- */
 

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libst.so")
-SOURCES = ("st_kernels.cu", "st_runtime.cu")
+SOURCES = ("st_kernels.cu", "st_runtime.cu", "st_static.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

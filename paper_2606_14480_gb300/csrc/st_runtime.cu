@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "st.h"
+#include "st_host.h"
 #include "st_kernels.cuh"
 
 using namespace st;
@@ -145,7 +146,7 @@ extern "C" void st_config_default(st_config* c) {
     c->cand_cap = 4096;
 }
 
-static bool derive_params(const st_config& c, DevParams& P, std::string& err) {
+bool derive_params(const st_config& c, DevParams& P, std::string& err) {
     std::memset(&P, 0, sizeof(P));
     auto fail = [&](const char* m) {
         err = m;

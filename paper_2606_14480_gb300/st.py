@@ -100,6 +100,8 @@ SIGNATURES = {
     "st_read_counters": ([_P, C.POINTER(StCounters), C.c_int], C.c_int),
     "st_set_timing": ([_P, C.c_int], C.c_int),
     "st_kernel_ms": ([_P, C.POINTER(C.c_float * 4)], C.c_int),
+    "seeding_run_static": ([C.POINTER(StConfig), C.POINTER(StHits), C.POINTER(StSeeds), _P, C.c_char_p,
+                            C.c_int32], C.c_int),
     "st_pipeline_config_default": ([C.POINTER(StPipelineConfig)], None),
     "st_pipeline_configure": ([_P, C.POINTER(StPipelineConfig)], C.c_int),
     "pipeline_submit": ([_P, C.POINTER(StHits), C.POINTER(StVelo), C.POINTER(C.c_uint64)], C.c_int),
@@ -383,6 +385,14 @@ class HostBuffers:
         return {"ev_off": self.ev_off.copy(), "hits": self.hits[:ns].copy(), "params": self.params[:ns].copy(),
                 "state": self.state[:ns].copy(), "n_hits": self.n_hits[:ns].copy(), "status": self.status[:n].copy(),
                 "velo_idx": self.velo_idx[:ns].copy(), "chi2": self.chi2[:ns].copy(), "n_long": self.n_long[:n].copy()}
+
+
+def seeding_run_static(cfg: StConfig, hits: StHits, seeds: StSeeds, stream=None) -> Tuple[int, str]:
+    """The allocation-free seeding entry point; returns (status, message)."""
+    buf = C.create_string_buffer(512)
+    rc = library().seeding_run_static(C.byref(cfg), C.byref(hits), C.byref(seeds), _stream_handle(stream), buf,
+                                      len(buf))
+    return rc, buf.value.decode()
 
 
 def run_batch(ctx: Context, db: DeviceBatch, cap: Optional[int] = None, stream=None) -> DeviceOutputs:
