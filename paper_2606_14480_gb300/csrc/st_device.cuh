@@ -42,6 +42,7 @@ struct DevParams {
     float xzb[6], xf_hi[6], xf_lo[6];
     // stereo-slot geometry (slots ordered by z)
     float uz[6], uzb[6], uf_hi[6], uf_lo[6], ut[6], uzt[6];
+    float uinv_t[6], uinv_z[6];  // 1/dxdy and 1/z of the stereo slots
     float zc_uv;           // centring z of the y-z line fit (uzt = uz - zc_uv)
     IterP it[2];
     int n_iter;

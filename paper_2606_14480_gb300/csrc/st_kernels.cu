@@ -35,13 +35,21 @@ __device__ __forceinline__ int64_t cont_base(const int64_t* ev_off, int64_t e) {
     return (b + 3) & ~int64_t(3);
 }
 
+// Sum per-thread counters over the CTA (warp shuffles, then shared memory)
+// and add them to the global counters with one atomic per counter per CTA.
+// Every thread of the CTA must call it.
 __device__ __forceinline__ void flush_counters(unsigned long long* dst, const ull* c, int n) {
+    __shared__ ull s_acc[16];
+    if (threadIdx.x < 16) s_acc[threadIdx.x] = 0;
+    __syncthreads();
     for (int k = 0; k < n; ++k) {
         ull v = c[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst + k, v);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_acc[k], v);
     }
+    __syncthreads();
+    if (threadIdx.x < n && s_acc[threadIdx.x]) atomicAdd(dst + threadIdx.x, s_acc[threadIdx.x]);
 }
 
 // ===========================================================================
@@ -166,6 +174,34 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
 // seeding
 // ===========================================================================
 
+// ---------------------------------------------------------------------------
+// per-zone bucket tables: lut[b] = first hit of the zone with bin(x) >= b, so
+// that a window edge is found with one table read and a short forward scan
+// (the same result as a binary search over the sorted zone)
+// ---------------------------------------------------------------------------
+
+constexpr float kLutRange = 4096.f;
+constexpr int kLutBins = 256;  // 32 mm buckets over [-4096, 4096) mm
+
+__device__ __forceinline__ int lut_bin(float v) {
+    const int b = __float2int_rd((v + kLutRange) * (kLutBins / (2.f * kLutRange)));
+    return min(max(b, 0), kLutBins - 1);
+}
+
+// first index i in [0, n) with x[i] >= v (n if none)
+__device__ __forceinline__ int zlo(const float* x, const uint16_t* lut, int n, float v) {
+    int i = lut[lut_bin(v)];
+    while (i < n && x[i] < v) ++i;
+    return i;
+}
+
+// first index i in [0, n) with x[i] > v (n if none)
+__device__ __forceinline__ int zhi(const float* x, const uint16_t* lut, int n, float v) {
+    int i = lut[lut_bin(v)];
+    while (i < n && !(v < x[i])) ++i;
+    return i;
+}
+
 struct Trip {
     int pos[6];
     float th[3], dth[3];
@@ -180,7 +216,7 @@ struct Trip {
 // correction dth = G y and the chi2 are then computed from small numbers.
 // Returns 0 (fewer than 5 hits), 1 (chi2 cut) or 2 (candidate).
 __device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, const int* szl,
-                          int k1, int k2, int k3, Trip& o) {
+                          const uint16_t* lut, int k1, int k2, int k3, Trip& o) {
     const int p1 = szl[I.s1] + k1, p2 = szl[I.s2] + k2, p3 = szl[I.s3] + k3;
     const float x1 = X[p1], x2 = X[p2], x3 = X[p3];
     const float t13 = (x3 - x1) * I.inv_dz31;
@@ -188,38 +224,38 @@ __device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, co
     const float c3 = (x2 - base) * I.inv_k3;
     const float b3 = fmaf(-c3, I.q31, t13);
     const float a3 = x1 - fmaf(c3, I.f1, b3 * I.zb1);
+    int nx = 3, m = 0;
 #pragma unroll
-    for (int s = 0; s < 6; ++s) o.pos[s] = -1;
-    o.pos[I.s1] = p1;
-    o.pos[I.s2] = p2;
-    o.pos[I.s3] = p3;
-    int nx = 3;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const int s = I.ext[j];
-        const float xp = fmaf(c3, P.xf_hi[s], fmaf(b3, P.xzb[s], a3));
-        const int st = szl[s], n = szl[s + 1] - st;
-        int k = lower_bound_f(X + st, n, xp - P.ext_tol);
-        int best = -1;
-        float bd = 0.f;
-        for (; k < n; ++k) {
-            const float xh = X[st + k];
-            if (xh > xp + P.ext_tol) break;
-            const float d = fabsf(xh - xp);
-            if (d <= P.ext_tol && (best < 0 || d < bd)) {
-                best = st + k;
-                bd = d;
+    for (int s = 0; s < 6; ++s) {
+        int p;
+        if (s == I.s1) {
+            p = p1;
+        } else if (s == I.s2) {
+            p = p2;
+        } else if (s == I.s3) {
+            p = p3;
+        } else {
+            const float xp = fmaf(c3, P.xf_hi[s], fmaf(b3, P.xzb[s], a3));
+            const int st = szl[s], n = szl[s + 1] - st;
+            const float* xs = X + st;
+            int k = zlo(xs, lut + s * kLutBins, n, xp - P.ext_tol);
+            p = -1;
+            float bd = 0.f;
+            for (; k < n; ++k) {
+                const float xh = xs[k];
+                if (xh > xp + P.ext_tol) break;
+                const float d = fabsf(xh - xp);
+                if (d <= P.ext_tol && (p < 0 || d < bd)) {
+                    p = st + k;
+                    bd = d;
+                }
             }
+            nx += p >= 0;
         }
-        if (best >= 0) {
-            o.pos[s] = best;
-            ++nx;
-        }
+        o.pos[s] = p;
+        m |= (p >= 0) << s;
     }
     if (nx < 5) return 0;
-    int m = 0;
-#pragma unroll
-    for (int s = 0; s < 6; ++s) m |= (o.pos[s] >= 0) << s;
     const int mi = P.mask_index[m];
     float y[6];
 #pragma unroll
@@ -249,7 +285,7 @@ __device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, co
         }
     }
     chi2 *= P.inv_sx2;
-    if (chi2 / static_cast<float>(nx - 3) > P.chi2x_max) return 1;
+    if (chi2 > P.chi2x_max * static_cast<float>(nx - 3)) return 1;
     o.th[0] = a3; o.th[1] = b3; o.th[2] = c3;
     o.dth[0] = da; o.dth[1] = db; o.dth[2] = dc;
     o.chi2 = chi2;
@@ -274,31 +310,35 @@ struct UV {
 // One UV combination (Section 3.4): start from the kinit-th hit of the
 // initial stereo layer of `pass`, ty from the origin, closest hit within
 // uv_tol in each remaining stereo layer in increasing z with ty averaging,
-// then (fit = true, n >= n_uv_min) the straight-line fit y = y0 + ty z.  The
-// y of each hit is formed as a float-float from error-free transformations
-// and fitted relative to the line y = tyr z, so chi2_y keeps ~1e-6 relative
-// accuracy.
-__device__ void uv_combo(const DevParams& P, const float* X, const int* szl, const float* th,
-                         const float* dth, int pass, int kinit, bool fit, UV& o) {
-#pragma unroll
-    for (int u = 0; u < 6; ++u) o.pos[u] = -1;
+// then (fit = true, n >= n_uv_min) the straight-line fit y = y0 + ty z.  A
+// combination that can no longer reach n_uv_min stops early (its result is
+// unused either way).  The y of each hit is formed as a float-float from
+// error-free transformations and fitted relative to the line y = tyr z, so
+// chi2_y keeps ~1e-6 relative accuracy.
+__device__ void uv_combo(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
+                         const float* th, const float* dth, int pass, int kinit, bool fit, UV& o) {
     const int ui = P.uv_init[pass];
     const int pi = szl[6 + ui] + kinit;
-    o.pos[ui] = pi;
-    const float yi = (x_at_uv(P, th, dth, ui) - X[pi]) / P.ut[ui];
-    float ty = yi / P.uz[ui];
+    const float yi = (x_at_uv(P, th, dth, ui) - X[pi]) * P.uinv_t[ui];
+    float ty = yi * P.uinv_z[ui];
     int n = 1;
+    o.n = 0;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        const int u = P.uv_rem[pass][q];
+    for (int u = 0; u < 6; ++u) {
+        o.pos[u] = -1;
+        if (u == ui) {
+            o.pos[u] = pi;
+            continue;
+        }
         const float Xl = x_at_uv(P, th, dth, u);
         const float xp = Xl - P.ut[u] * ty * P.uz[u];
         const int st = szl[6 + u], nn = szl[7 + u] - st;
-        int k = lower_bound_f(X + st, nn, xp - P.uv_tol);
+        const float* xs = X + st;
+        int k = zlo(xs, lut + (6 + u) * kLutBins, nn, xp - P.uv_tol);
         int best = -1;
         float bd = 0.f;
         for (; k < nn; ++k) {
-            const float xh = X[st + k];
+            const float xh = xs[k];
             if (xh > xp + P.uv_tol) break;
             const float d = fabsf(xh - xp);
             if (d <= P.uv_tol && (best < 0 || d < bd)) {
@@ -307,10 +347,15 @@ __device__ void uv_combo(const DevParams& P, const float* X, const int* szl, con
             }
         }
         if (best >= 0) {
-            const float yl = (Xl - X[best]) / P.ut[u];
-            ty = 0.5f * (ty + yl / P.uz[u]);
+            const float yl = (Xl - X[best]) * P.uinv_t[u];
+            ty = 0.5f * fmaf(yl, P.uinv_z[u], ty);
             o.pos[u] = best;
             ++n;
+        }
+        const int rem = (5 - u) - (ui > u ? 1 : 0);  // stereo layers still to search
+        if (n + rem < P.n_uv_min) {
+            o.n = n;
+            return;
         }
     }
     o.n = n;
@@ -320,12 +365,11 @@ __device__ void uv_combo(const DevParams& P, const float* X, const int* szl, con
     o.wm = 0.f;
     o.zm = 0.f;
     if (!fit || n < P.n_uv_min) return;
-    float w[6], zt[6];
+    float w[6];
     float sw = 0.f, sz = 0.f;
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
         w[u] = 0.f;
-        zt[u] = P.uzt[u];
         if (o.pos[u] < 0) continue;
         const float xh = X[o.pos[u]];
         // D = x(z_u) - x_hit as hi + lo
@@ -337,14 +381,15 @@ __device__ void uv_combo(const DevParams& P, const float* X, const int* szl, con
         two_sum(s2, p2, s3, e3);
         const float lo = ((e + pe) + (e2 + pe2)) + (e3 + fmaf(th[2], P.uf_lo[u],
                           fmaf(dth[2], P.uf_hi[u], fmaf(dth[1], P.uzb[u], dth[0]))));
-        // y = D / t
-        const float t = P.ut[u];
-        const float yh = s3 / t;
-        const float rem = fmaf(-yh, t, s3);
-        const float yl = (rem + lo) / t;
+        // y = D / t as hi + lo: the remainder of the rounded quotient is exact,
+        // so a reciprocal multiply loses nothing
+        const float t = P.ut[u], it = P.uinv_t[u];
+        const float yh = s3 * it;
+        const float rm = fmaf(-yh, t, s3);
+        const float yl = (rm + lo) * it;
         w[u] = fmaf(-ty, P.uz[u], yh) + yl;
         sw += w[u];
-        sz += zt[u];
+        sz += P.uzt[u];
     }
     const float inv_n = 1.f / static_cast<float>(n);
     const float wm = sw * inv_n, zm = sz * inv_n;
@@ -352,7 +397,7 @@ __device__ void uv_combo(const DevParams& P, const float* X, const int* szl, con
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
         if (o.pos[u] < 0) continue;
-        const float dz = zt[u] - zm;
+        const float dz = P.uzt[u] - zm;
         szz = fmaf(dz, dz, szz);
         szw = fmaf(dz, w[u] - wm, szw);
     }
@@ -361,7 +406,7 @@ __device__ void uv_combo(const DevParams& P, const float* X, const int* szl, con
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
         if (o.pos[u] < 0) continue;
-        const float r = (w[u] - wm) - beta * (zt[u] - zm);
+        const float r = (w[u] - wm) - beta * (P.uzt[u] - zm);
         chi2 = fmaf(r, r, chi2);
     }
     o.chi2 = chi2 * P.inv_sy2;
@@ -379,48 +424,69 @@ __device__ __forceinline__ ull pack_trip(int it, int k1, int k3, int k2) {
     return (ull(it) << 60) | (ull(k1) << 40) | (ull(k3) << 20) | ull(k2);
 }
 
+// The two-hit / third-hit windows of one pair: first T2 index and count.
+__device__ __forceinline__ int pair_window(const DevParams& P, const IterP& I, const float* X,
+                                           const int* szl, const uint16_t* lut, float x1, float x3,
+                                           int& lo2) {
+    const float t13 = (x3 - x1) * I.inv_dz31;
+    const float x0 = fmaf(-I.z1, t13, x1);
+    const float ip = fmaf(P.invp_b * x0, x0, P.invp_a * fabsf(x0));
+    lo2 = 0;
+    if (!(ip > 0.f)) return 0;
+    const float sg = x0 > 0.f ? 1.f : -1.f;
+    const float ulo = fmaf(I.mlo_k, ip, -I.c0), uhi = fmaf(I.mhi_k, ip, I.c0);
+    const float bs = fmaf(I.dz21, t13, x1);
+    const float xa = fmaf(I.k3, -sg * ulo, bs), xb = fmaf(I.k3, -sg * uhi, bs);
+    const int st2 = szl[I.s2], n2 = szl[I.s2 + 1] - st2;
+    const uint16_t* l2 = lut + I.s2 * kLutBins;
+    lo2 = zlo(X + st2, l2, n2, fminf(xa, xb));
+    return zhi(X + st2, l2, n2, fmaxf(xa, xb)) - lo2;
+}
+
+constexpr int kTripPerCand = 2;  // triplet buffer entries per candidate slot
+
 size_t seed_smem_bytes(int threads, int smem_hits, int tbl_smem, int key_smem) {
-    return align16(sizeof(float) * smem_hits) + sizeof(ull) * (tbl_smem + key_smem) +
-           sizeof(ull) * 2 * threads + sizeof(int) * 7 * threads + sizeof(int) * (36 + 16);
+    return align16(sizeof(float) * smem_hits) + align16(sizeof(uint16_t) * 12 * kLutBins) +
+           sizeof(ull) * (tbl_smem + key_smem) + sizeof(int) * 3 * threads + sizeof(int) * (36 + 16);
 }
 
 size_t seed_slot_bytes(int cand_cap, int max_xhits) {
-    return align16(sizeof(int) * 16 * size_t(cand_cap)) + sizeof(ull) * (size_t(max_xhits) + cand_cap);
+    return align16(sizeof(int) * 16 * size_t(cand_cap)) +
+           sizeof(ull) * (size_t(max_xhits) + cand_cap + size_t(kTripPerCand) * cand_cap);
 }
 
-__global__ void __launch_bounds__(kMaxThreads)
+// two CTAs of 512 threads (four of 256) per SM: 64 registers per thread
+__global__ void __launch_bounds__(kMaxThreads, 2)
 k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = blockDim.x, tid = threadIdx.x;
     unsigned char* sp = smem;
     float* sx = reinterpret_cast<float*>(sp);
     sp += align16(sizeof(float) * A.smem_hits);
+    uint16_t* lut = reinterpret_cast<uint16_t*>(sp);
+    sp += align16(sizeof(uint16_t) * 12 * kLutBins);
     ull* stab = reinterpret_cast<ull*>(sp);
     sp += sizeof(ull) * A.tbl_smem;
     ull* skey = reinterpret_cast<ull*>(sp);
     sp += sizeof(ull) * A.key_smem;
-    ull* fifo = reinterpret_cast<ull*>(sp);
-    sp += sizeof(ull) * 2 * T;
     int* sPS = reinterpret_cast<int*>(sp);
     int* sA = sPS + T;
     int* sB = sA + T;
-    int* sTS = sB + T;
-    int* sTA = sTS + T;
-    int* sTB = sTA + T;
-    int* sTC = sTB + T;
-    int* tmp = sTC + T;
+    int* tmp = sB + T;
     int* szl = tmp + 36;
     __shared__ int s_item;
     __shared__ ull s_start;
 
     const int CC = A.cand_cap;
+    const int TC = kTripPerCand * CC;
     uint8_t* slot = A.slot + int64_t(blockIdx.x) * A.slot_stride;
-    int* c_pos = reinterpret_cast<int*>(slot);           // [6][CC]
+    int* c_pos = reinterpret_cast<int*>(slot);               // [6][CC]
     float* c_f = reinterpret_cast<float*>(c_pos + 6 * CC);  // [8][CC]: th0..2, dth0..2, chi2, score
     int* c_nx = reinterpret_cast<int*>(c_f + 8 * CC);
     int* kept = c_nx + CC;
     ull* g_tbl = reinterpret_cast<ull*>(slot + align16(sizeof(int) * 16 * size_t(CC)));
     ull* g_key = g_tbl + A.max_xhits;
+    ull* trip = g_key + CC;
 
     ull ctr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
@@ -447,45 +513,33 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
         }
         __syncthreads();
 
-        // ------------------------------------------------------------ XZ
-        int ncand = 0, nfifo = 0;
-        auto flush = [&](int m) {
-            Trip o;
-            int code = -1;
-            if (tid < m) {
-                const ull tk = fifo[tid];
-                const int it = static_cast<int>(tk >> 60);
-                code = do_triplet(P, P.it[it], X, szl, static_cast<int>((tk >> 40) & 0xFFFFF),
-                                  static_cast<int>(tk & 0xFFFFF), static_cast<int>((tk >> 20) & 0xFFFFF), o);
-                ctr[2] += code >= 1;
-            }
-            int tot;
-            const int co = block_exscan(code == 2 ? 1 : 0, tmp, tot);
-            if (code == 2) {
-                const int ci = ncand + co;
-                if (ci < CC) {
+        // ------------------------------------------------------------ bucket tables
+        for (int g = tid; g < nh; g += T) {
+            int z = 0;
 #pragma unroll
-                    for (int s = 0; s < 6; ++s) c_pos[s * CC + ci] = o.pos[s];
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        c_f[q * CC + ci] = o.th[q];
-                        c_f[(3 + q) * CC + ci] = o.dth[q];
-                    }
-                    c_f[6 * CC + ci] = o.chi2;
-                    c_f[7 * CC + ci] = o.score;
-                    c_nx[ci] = o.nx;
-                }
-            }
-            ncand += tot;
-            const int rem = nfifo - m;
-            ull v = 0;
-            if (tid < rem) v = fifo[m + tid];
-            __syncthreads();
-            if (tid < rem) fifo[tid] = v;
-            nfifo = rem;
-            __syncthreads();
-        };
+            for (int q = 1; q < 12; ++q) z += g >= szl[q];
+            const int st = szl[z], n = szl[z + 1] - st, i = g - st;
+            uint16_t* lz = lut + z * kLutBins;
+            const int b = lut_bin(X[g]);
+            const int bp = i == 0 ? -1 : lut_bin(X[g - 1]);
+            for (int q = bp + 1; q <= b; ++q) lz[q] = static_cast<uint16_t>(i);
+            if (i == n - 1)
+                for (int q = b + 1; q < kLutBins; ++q) lz[q] = static_cast<uint16_t>(n);
+        }
+        for (int k = tid; k < 12 * kLutBins; k += T) {
+            const int z = k / kLutBins;
+            if (szl[z + 1] == szl[z]) lut[k] = 0;
+        }
+        __syncthreads();
 
+        // ------------------------------------------------------------ XZ
+        // Each round takes up to T first hits (iteration 0's T1 layer, then
+        // iteration 1's), expands their T3 windows into pairs, and each thread
+        // walks a contiguous range of the round's pairs twice: once to count
+        // its triplets, once (after a block scan) to write them in order into
+        // the round's triplet buffer; the triplets then become candidates.
+        int ncand = 0;
+        bool overflow = false;
         const int n1_0 = szl[P.it[0].s1 + 1] - szl[P.it[0].s1];
         const int n1_1 = P.n_iter > 1 ? szl[P.it[1].s1 + 1] - szl[P.it[1].s1] : 0;
         const int n_items = n1_0 + n1_1;
@@ -499,8 +553,9 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 const float x1 = X[szl[I.s1] + k1];
                 const float xc = I.scale3 * x1;
                 const int st3 = szl[I.s3], n3 = szl[I.s3 + 1] - st3;
-                lo3 = lower_bound_f(X + st3, n3, xc - I.dx3);
-                np = upper_bound_f(X + st3, n3, xc + I.dx3) - lo3;
+                const uint16_t* l3 = lut + I.s3 * kLutBins;
+                lo3 = zlo(X + st3, l3, n3, xc - I.dx3);
+                np = zhi(X + st3, l3, n3, xc + I.dx3) - lo3;
                 tag = (it << 20) | k1;
             }
             ctr[0] += np;
@@ -510,58 +565,87 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             sA[tid] = lo3;
             sB[tid] = tag;
             __syncthreads();
-            for (int pb = 0; pb < tot_p; pb += T) {
-                const int pidx = pb + tid;
-                int nt = 0, lo2 = 0, ptag = 0, k3 = 0;
-                if (pidx < tot_p) {
-                    const int o = owner_of(sPS, T, pidx);
-                    const int tg = sB[o];
-                    const int it = tg >> 20, k1 = tg & 0xFFFFF;
-                    k3 = sA[o] + (pidx - sPS[o]);
+            int ntrip = 0;
+            const int pb = static_cast<int>((int64_t(tot_p) * tid) / T);
+            const int pe = static_cast<int>((int64_t(tot_p) * (tid + 1)) / T);
+            // walk [pb, pe): pass 0 counts, pass 1 writes
+            int nt = 0, wofs = 0;
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 1) {
+                    int tot_t;
+                    wofs = block_exscan(nt, tmp, tot_t);
+                    ctr[1] += nt;
+                    if (ntrip + tot_t > TC) overflow = true;
+                    if (overflow) break;
+                    wofs += ntrip;
+                    ntrip += tot_t;
+                }
+                if (pb >= pe) continue;
+                int o = owner_of(sPS, T, pb);
+                int nxt = o + 1 < T ? sPS[o + 1] : tot_p;
+                int k3 = sA[o] + (pb - sPS[o]);
+                int tg = sB[o];
+                int it = tg >> 20, k1 = tg & 0xFFFFF;
+                float x1 = X[szl[P.it[it].s1] + k1];
+                int w = 0;
+                for (int p = pb; p < pe; ++p) {
+                    while (p >= nxt) {
+                        ++o;
+                        nxt = o + 1 < T ? sPS[o + 1] : tot_p;
+                        k3 = sA[o];
+                        tg = sB[o];
+                        it = tg >> 20;
+                        k1 = tg & 0xFFFFF;
+                        x1 = X[szl[P.it[it].s1] + k1];
+                    }
                     const IterP& I = P.it[it];
-                    const float x1 = X[szl[I.s1] + k1], x3 = X[szl[I.s3] + k3];
-                    const float t13 = (x3 - x1) * I.inv_dz31;
-                    const float x0 = fmaf(-I.z1, t13, x1);
-                    const float ip = fmaf(P.invp_b * x0, x0, P.invp_a * fabsf(x0));
-                    if (ip > 0.f) {
-                        const float sg = x0 > 0.f ? 1.f : -1.f;
-                        const float ulo = fmaf(I.mlo_k, ip, -I.c0), uhi = fmaf(I.mhi_k, ip, I.c0);
-                        const float bs = fmaf(I.dz21, t13, x1);
-                        const float xa = fmaf(I.k3, -sg * ulo, bs), xb = fmaf(I.k3, -sg * uhi, bs);
-                        const int st2 = szl[I.s2], n2 = szl[I.s2 + 1] - st2;
-                        lo2 = lower_bound_f(X + st2, n2, fminf(xa, xb));
-                        nt = upper_bound_f(X + st2, n2, fmaxf(xa, xb)) - lo2;
-                    }
-                    ptag = tg;
+                    int lo2;
+                    const int c = pair_window(P, I, X, szl, lut, x1, X[szl[I.s3] + k3], lo2);
+                    if (pass == 1)
+                        for (int q = 0; q < c; ++q) trip[wofs + w + q] = pack_trip(it, k1, k3, lo2 + q);
+                    w += c;
+                    ++k3;
                 }
-                ctr[1] += nt;
-                int tot_t;
-                const int ts = block_exscan(nt, tmp, tot_t);
-                sTS[tid] = ts;
-                sTA[tid] = lo2;
-                sTB[tid] = ptag;
-                sTC[tid] = k3;
-                __syncthreads();
-                for (int tb = 0; tb < tot_t; tb += T) {
-                    const int t = tb + tid;
-                    const int m = min(T, tot_t - tb);
-                    if (t < tot_t) {
-                        const int o = owner_of(sTS, T, t);
-                        const int tg = sTB[o];
-                        fifo[nfifo + (t - tb)] = pack_trip(tg >> 20, tg & 0xFFFFF, sTC[o], sTA[o] + (t - sTS[o]));
-                    }
-                    nfifo += m;
-                    __syncthreads();
-                    if (nfifo >= T) flush(T);
-                }
-                __syncthreads();
+                if (pass == 0) nt = w;
             }
             __syncthreads();
+            if (overflow) break;
+
+            // this round's triplets -> candidates, in order
+            for (int b = 0; b < ntrip; b += T) {
+                const int t = b + tid;
+                Trip o;
+                int code = -1;
+                if (t < ntrip) {
+                    const ull tk = trip[t];
+                    const int it = static_cast<int>(tk >> 60);
+                    code = do_triplet(P, P.it[it], X, szl, lut, static_cast<int>((tk >> 40) & 0xFFFFF),
+                                      static_cast<int>(tk & 0xFFFFF), static_cast<int>((tk >> 20) & 0xFFFFF), o);
+                    ctr[2] += code >= 1;
+                }
+                int tot;
+                const int co = block_exscan(code == 2 ? 1 : 0, tmp, tot);
+                if (code == 2) {
+                    const int ci = ncand + co;
+                    if (ci < CC) {
+#pragma unroll
+                        for (int s = 0; s < 6; ++s) c_pos[s * CC + ci] = o.pos[s];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            c_f[q * CC + ci] = o.th[q];
+                            c_f[(3 + q) * CC + ci] = o.dth[q];
+                        }
+                        c_f[6 * CC + ci] = o.chi2;
+                        c_f[7 * CC + ci] = o.score;
+                        c_nx[ci] = o.nx;
+                    }
+                }
+                ncand += tot;
+            }
         }
-        if (nfifo > 0) flush(nfifo);
         if (tid == 0) ctr[3] += ncand;
 
-        if (ncand > CC) {
+        if (overflow || ncand > CC) {
             if (tid == 0) {
                 A.status[e] = -3;  // ST_OVERFLOW
                 A.item_count[item] = 0;
@@ -623,8 +707,9 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 const float t = P.ut[ui];
                 const float xa = fmaf(-P.uv_yhi[h], t, Xi), xb = fmaf(-P.uv_ylo[h], t, Xi);
                 const int st = szl[6 + ui], n = szl[7 + ui] - st;
-                lo = lower_bound_f(X + st, n, fminf(xa, xb));
-                cntc = upper_bound_f(X + st, n, fmaxf(xa, xb)) - lo;
+                const uint16_t* lz = lut + (6 + ui) * kLutBins;
+                lo = zlo(X + st, lz, n, fminf(xa, xb));
+                cntc = zhi(X + st, lz, n, fmaxf(xa, xb)) - lo;
             }
             ctr[5] += cntc;
             int tot;
@@ -633,22 +718,30 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             sA[tid] = lo;
             sB[tid] = i;
             __syncthreads();
-            for (int cb = 0; cb < tot; cb += T) {
-                const int c = cb + tid;
-                if (c < tot) {
-                    const int o = owner_of(sPS, T, c);
+            const int cb = static_cast<int>((int64_t(tot) * tid) / T);
+            const int ce = static_cast<int>((int64_t(tot) * (tid + 1)) / T);
+            if (cb < ce) {
+                int o = owner_of(sPS, T, cb);
+                int nxt = o + 1 < T ? sPS[o + 1] : tot;
+                int kinit = sA[o] + (cb - sPS[o]);
+                for (int c = cb; c < ce; ++c) {
+                    while (c >= nxt) {
+                        ++o;
+                        nxt = o + 1 < T ? sPS[o + 1] : tot;
+                        kinit = sA[o];
+                    }
                     const int it2 = sB[o];
                     const int j = it2 >> 1, pass = it2 & 1;
-                    const int kinit = sA[o] + (c - sPS[o]);
                     const int k = kept[j];
                     const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
                     const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
                     UV u;
-                    uv_combo(P, X, szl, th, dth, pass, kinit, true, u);
+                    uv_combo(P, X, szl, lut, th, dth, pass, kinit, true, u);
                     if (u.n >= P.n_uv_min) {
                         ++ctr[6];
                         atomicMin(&ukey[j], uv_key(u.n, u.chi2, pass, kinit));
                     }
+                    ++kinit;
                 }
             }
             __syncthreads();
@@ -692,7 +785,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
                 const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
                 UV u;
-                uv_combo(P, X, szl, th, dth, pass, kinit, true, u);
+                uv_combo(P, X, szl, lut, th, dth, pass, kinit, true, u);
                 int32_t* ho = A.pool_hits + r * 12;
 #pragma unroll
                 for (int s = 0; s < 6; ++s) {
@@ -768,13 +861,50 @@ __global__ void __launch_bounds__(256) k_gather(const __grid_constant__ GatherAr
 // matching
 // ===========================================================================
 
-size_t match_smem_bytes(int velo_smem) { return sizeof(float) * 7 * size_t(velo_smem); }
+constexpr int kTyBins = 64;
+constexpr float kTyRange = 0.32f;  // buckets of 0.01 over [-0.32, 0.32); outside values go to the end buckets
 
+size_t match_smem_bytes(int velo_smem) {
+    return sizeof(float) * 7 * size_t(velo_smem) + sizeof(int) * (size_t(velo_smem) + 2 * kTyBins + 8);
+}
+
+__device__ __forceinline__ int ty_bin(float ty) {
+    const int b = __float2int_rd((ty + kTyRange) * (kTyBins / (2.f * kTyRange)));
+    return min(max(b, 0), kTyBins - 1);  // NaN maps to bucket 0 and never passes the cuts
+}
+
+// One (VELO, seed) pair of Section 4: preselection, then chi2_match; updates
+// the best (chi2, VELO index).  Position differences are formed from
+// float-float extrapolations to z = A_x and z = z_match_y.
+__device__ __forceinline__ int match_pair(const DevParams& P, float vxh, float vxl, float vyh, float vyl,
+                                          float vtx, float vty, float vit, int vg, float xh, float xl,
+                                          float yh, float yl, float txS, float tyS, float dzx, float& best,
+                                          int& bv) {
+    const float dtx = vtx - txS, dty = vty - tyS;
+    if (!(fabsf(dty) < P.cut_ty) || !(fabsf(dtx) < P.cut_tx)) return 0;
+    const float dy = (vyh - yh) + (vyl - yl);
+    if (!(fabsf(dy) < P.cut_y)) return 0;
+    const float dz = fmaf(P.Bx, fabsf(dtx), fmaf(P.Cx, dtx * dtx, fmaf(P.Ex * vtx, vtx, dzx)));
+    const float dx = fmaf(dz, dtx, (vxh - xh) + (vxl - xl));
+    if (!(fabsf(dx) < P.cut_x)) return 0;
+    const float tolx = fmaf(P.tolx_b, dtx * dtx, P.tolx_a);
+    const float c2 = dx * dx / tolx + dy * dy * vit + dtx * dtx * P.inv_toltx + dty * dty * P.inv_tolty;
+    if (c2 < P.chi2m_max && (c2 < best || (c2 == best && vg < bv))) {
+        best = c2;
+        bv = vg;
+    }
+    return 1;
+}
+
+// One event per work item; one thread per seed.  The event's VELO segments
+// are staged in shared memory with their float-float extrapolations and
+// bucketed by ty, so a seed only visits the buckets its |dty| cut can reach
+// (every other pair fails that cut).  Events with more segments than fit are
+// processed in chunks, each scanned in full.
 __global__ void __launch_bounds__(kMaxThreads)
 k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int VS = A.velo_smem, T = blockDim.x, tid = threadIdx.x;
-    const int lane = tid & 31, wid = tid >> 5, nwarp = T >> 5;
     float* vxh = reinterpret_cast<float*>(smem);
     float* vxl = vxh + VS;
     float* vyh = vxl + VS;
@@ -782,6 +912,9 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
     float* vtx = vyl + VS;
     float* vty = vtx + VS;
     float* vit = vty + VS;
+    int* bidx = reinterpret_cast<int*>(vit + VS);  // VELO indices grouped by ty bucket
+    int* bcnt = bidx + VS;                         // [kTyBins]
+    int* boff = bcnt + kTyBins;                    // [kTyBins + 1]
     __shared__ int s_item, s_cnt;
     ull ctr[3] = {0, 0, 0};
 
@@ -798,8 +931,11 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
         const int nv = static_cast<int>(A.velo_off[e + 1] - v0);
         const int64_t s0 = A.seed_off[e];
         const int ns = A.seed_off[e + 1] - static_cast<int>(s0);
+        const bool bucketed = nv <= VS;
         for (int vc = 0; vc < nv; vc += VS) {
             const int m = min(VS, nv - vc);
+            for (int k = tid; k < kTyBins; k += T) bcnt[k] = 0;
+            __syncthreads();
             for (int v = tid; v < m; v += T) {
                 const float* st = A.velo + (v0 + vc + v) * 4;
                 const float x = st[0], y = st[1], tx = st[2], ty = st[3];
@@ -815,9 +951,30 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
                 vtx[v] = tx;
                 vty[v] = ty;
                 vit[v] = 1.f / fmaf(P.toly_b, fmaf(tx, tx, ty * ty), P.toly_a);
+                if (bucketed) atomicAdd(&bcnt[ty_bin(ty)], 1);
             }
             __syncthreads();
-            for (int s = wid; s < ns; s += nwarp) {
+            if (bucketed) {
+                if (tid < 32) {  // exclusive scan of the bucket counts by one warp
+                    int c0 = bcnt[2 * tid], c1 = bcnt[2 * tid + 1];
+                    int x = c0 + c1;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (tid >= o) x += y;
+                    }
+                    const int ex = x - c0 - c1;
+                    boff[2 * tid] = ex;
+                    boff[2 * tid + 1] = ex + c0;
+                    if (tid == 31) boff[kTyBins] = x;
+                }
+                __syncthreads();
+                for (int q = tid; q < kTyBins; q += T) bcnt[q] = boff[q];  // reuse as fill cursors
+                __syncthreads();
+                for (int v = tid; v < m; v += T) bidx[atomicAdd(&bcnt[ty_bin(vty[v])], 1)] = v;
+                __syncthreads();
+            }
+            for (int s = tid; s < ns; s += T) {
                 const float* st = A.seed_state + (s0 + s) * 4;
                 const float xS = st[0], yS = st[1], txS = st[2], tyS = st[3];
                 float p, pe, xh, xl, yh, yl;
@@ -829,45 +986,35 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
                 yl += fmaf(P.dMS_lo, tyS, pe);
                 const float dzx = P.Dx * fabsf(xS);
                 float best = FLT_MAX;
-                int bv = -1;
+                int bv = 0x7fffffff;
                 if (vc > 0) {
-                    bv = A.velo_idx[s0 + s];
-                    best = bv >= 0 ? A.chi2[s0 + s] : FLT_MAX;
+                    const int pv = A.velo_idx[s0 + s];
+                    if (pv >= 0) {
+                        bv = pv;
+                        best = A.chi2[s0 + s];
+                    }
                 }
                 int npre = 0;
-                for (int v = lane; v < m; v += 32) {
-                    const float dtx = vtx[v] - txS, dty = vty[v] - tyS;
-                    if (!(fabsf(dty) < P.cut_ty) || !(fabsf(dtx) < P.cut_tx)) continue;
-                    const float dy = (vyh[v] - yh) + (vyl[v] - yl);
-                    if (!(fabsf(dy) < P.cut_y)) continue;
-                    const float dz = fmaf(P.Bx, fabsf(dtx), fmaf(P.Cx, dtx * dtx, fmaf(P.Ex * vtx[v], vtx[v], dzx)));
-                    const float dx = fmaf(dz, dtx, (vxh[v] - xh) + (vxl[v] - xl));
-                    if (!(fabsf(dx) < P.cut_x)) continue;
-                    ++npre;
-                    const float tolx = fmaf(P.tolx_b, dtx * dtx, P.tolx_a);
-                    const float c2 = dx * dx / tolx + dy * dy * vit[v] + dtx * dtx * P.inv_toltx +
-                                     dty * dty * P.inv_tolty;
-                    const int vg = vc + v;
-                    if (c2 < P.chi2m_max && c2 < best) {
-                        best = c2;
-                        bv = vg;
+                if (bucketed) {
+                    // buckets that can hold |ty - tyS| < cut_ty (slightly widened;
+                    // the exact cut is applied per pair)
+                    const float w = P.cut_ty + 1e-6f * (fabsf(tyS) + P.cut_ty);
+                    const int k0 = boff[ty_bin(tyS - w)], k1 = boff[ty_bin(tyS + w) + 1];
+                    for (int k = k0; k < k1; ++k) {
+                        const int v = bidx[k];
+                        npre += match_pair(P, vxh[v], vxl[v], vyh[v], vyl[v], vtx[v], vty[v], vit[v], vc + v,
+                                           xh, xl, yh, yl, txS, tyS, dzx, best, bv);
                     }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                    if (ob < best || (ob == best && ov >= 0 && (bv < 0 || ov < bv))) {
-                        best = ob;
-                        bv = ov;
-                    }
+                } else {
+                    for (int v = 0; v < m; ++v)
+                        npre += match_pair(P, vxh[v], vxl[v], vyh[v], vyl[v], vtx[v], vty[v], vit[v], vc + v,
+                                           xh, xl, yh, yl, txS, tyS, dzx, best, bv);
                 }
                 ctr[1] += npre;
-                if (lane == 0) {
-                    A.velo_idx[s0 + s] = bv;
-                    A.chi2[s0 + s] = bv >= 0 ? best : 0.f;
-                    ctr[0] += m;
-                }
+                ctr[0] += m;
+                const bool found = best < FLT_MAX;
+                A.velo_idx[s0 + s] = found ? bv : -1;
+                A.chi2[s0 + s] = found ? best : 0.f;
             }
             __syncthreads();
         }
@@ -910,7 +1057,7 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
         int nl = 0;
         for (int s = tid; s < ns; s += T) nl += A.velo_idx[s0 + s] >= 0;
         nl = warp_sum(nl);
-        if (lane == 0 && nl) atomicAdd(&s_cnt, nl);
+        if ((tid & 31) == 0 && nl) atomicAdd(&s_cnt, nl);
         __syncthreads();
         if (tid == 0) {
             if (A.n_long) A.n_long[e] = s_cnt;

@@ -191,6 +191,8 @@ bool derive_params(const st_config& c, DevParams& P, std::string& err) {
         split(F(z), P.uf_hi[u], P.uf_lo[u]);
         P.ut[u] = static_cast<float>(c.dxdy[kUL[u]]);
         P.uzt[u] = static_cast<float>(z - zc);
+        P.uinv_t[u] = static_cast<float>(1.0 / c.dxdy[kUL[u]]);
+        P.uinv_z[u] = static_cast<float>(1.0 / z);
     }
     P.n_iter = c.n_iter;
     for (int it = 0; it < c.n_iter; ++it) {
