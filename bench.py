@@ -481,7 +481,7 @@ def serve(st, cfg, batched_rate, args, local):
                             return
                         time.sleep(0.0002)
                     info = poll_grow(st, ctx, tickets[i], int(sizes[i]))
-                    lat[i] = (info.t_done_ns - info.t_submit_ns) / 1e6
+                    lat[i] = (info.t_returned_ns - info.t_submit_ns) / 1e6
             except Exception as exc:  # surfaced by the main thread
                 errors.append(exc)
             finally:

@@ -291,28 +291,34 @@ void st_pipeline_config_default(st_pipeline_config* pc);
 int st_pipeline_configure(st_ctx* ctx, const st_pipeline_config* pc);
 
 /* Queue one batch given in HOST memory (hits->x, zone, ev_off etc. and
- * velo->state, ev_off are host pointers; z/dxdy ignored).  The data are
- * copied before the call returns, so the caller may reuse its buffers.
- * Batches are admitted to the device as slots and memory free up, packed with
- * other waiting batches into one launch, and overlap on the device.
- * *ticket identifies the batch.  ST_OVERFLOW if the batch can never fit a
- * slot; ST_ESTATE after st_destroy has begun. */
+ * velo->state, ev_off are host pointers; z/dxdy ignored).  The hits and VELO
+ * states are copied by DMA into device-resident input rings before the call
+ * returns, so the caller may reuse its buffers; if the rings are full the
+ * call waits (up to 60 s, then ST_TIMEOUT) until earlier batches have run.
+ * Waiting batches that follow each other in the rings are packed into one
+ * launch on a free slot; slots run on their own streams and overlap on the
+ * device.  *ticket identifies the batch.  ST_OVERFLOW if the batch can never
+ * fit a slot; ST_ESTATE after st_destroy has begun.  Results stay in a device
+ * output ring until polled: poll every ticket. */
 int pipeline_submit(st_ctx* ctx, const st_hits* host_hits, const st_velo* host_velo,
                     uint64_t* ticket);
 
-/* Timing of a finished request (host steady clock, nanoseconds). */
+/* Timing of a finished request (host steady clock, nanoseconds): submitted,
+ * launched on the device, results complete on the device, results copied
+ * into the caller's buffers by pipeline_poll. */
 typedef struct {
-    int64_t t_submit_ns, t_launch_ns, t_done_ns;
+    int64_t t_submit_ns, t_launch_ns, t_done_ns, t_returned_ns;
     int32_t n_events, n_seeds;
 } st_request_info;
 
 /* Wait up to timeout_us (0 = do not wait, < 0 = forever) for the batch of
- * `ticket`.  On ST_OK its seeds and Long tracks are copied into the HOST
- * buffers host_seeds (cap, ev_off, hits, params, state, n_hits, status) and
- * host_long (velo_idx, chi2, n_long; may be NULL), info (may be NULL) is
- * filled, and the ticket is released.  ST_PENDING (timeout_us == 0) or
- * ST_TIMEOUT if not ready; ST_OVERFLOW if host_seeds->cap is too small
- * (ticket kept); ST_EINVAL for an unknown ticket. */
+ * `ticket`.  On ST_OK its seeds and Long tracks are copied by DMA from the
+ * device output ring into the HOST buffers host_seeds (cap, ev_off, hits,
+ * params, state, n_hits, status) and host_long (velo_idx, chi2, n_long; may
+ * be NULL), info (may be NULL) is filled, and the ticket is released.
+ * ST_PENDING (timeout_us == 0) or ST_TIMEOUT if not ready; ST_OVERFLOW if
+ * host_seeds->cap is too small (ticket kept); ST_EINVAL for an unknown
+ * ticket. */
 int pipeline_poll(st_ctx* ctx, uint64_t ticket, st_seeds* host_seeds, st_long* host_long,
                   int64_t timeout_us, st_request_info* info);
 

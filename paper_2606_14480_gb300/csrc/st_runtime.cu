@@ -827,17 +827,85 @@ extern "C" void st_graph_destroy(st_graph* g) {
 // ---------------------------------------------------------------------------
 // serving pipeline
 // ---------------------------------------------------------------------------
+// What the pipeline keeps between calls lives in device memory:
+//  * input rings (hits: x and zone side by side; VELO states), filled by DMA
+//    straight from the caller's memory inside pipeline_submit;
+//  * an output ring, one block per launch, written by the kernels and read
+//    by DMA straight into the caller's memory inside pipeline_poll.
+// The host never copies event data.  A dispatcher thread packs waiting
+// requests that follow each other in the input rings into one launch on a
+// free slot (stream + workspace); a completer thread retires launches in
+// order.
+
+// FIFO ring allocator over `cap` units; blocks are released by id in any
+// order and their space is reclaimed from the oldest block on.  Blocks are
+// exact (no padding), so consecutive blocks are contiguous unless the ring
+// wrapped.  Zero-size blocks take no space.
+struct Ring {
+    size_t cap = 0, head = 0;
+    uint64_t next_id = 1;
+    struct B {
+        uint64_t id;
+        size_t off, size;
+        bool released;
+    };
+    std::deque<B> live;
+
+    bool alloc(size_t n, size_t& off, uint64_t& id) {
+        if (n > cap) return false;
+        const B* oldest = nullptr;
+        for (const auto& b : live)
+            if (b.size > 0) {
+                oldest = &b;
+                break;
+            }
+        if (!oldest) {
+            if (head + n > cap) head = 0;
+            off = head;
+        } else {
+            const size_t tail = oldest->off;
+            if (head > tail) {  // occupied: [tail, head)
+                if (head + n <= cap) off = head;
+                else if (n <= tail) off = 0;
+                else return false;
+            } else {            // occupied: [tail, cap) and [0, head)
+                if (head + n <= tail) off = head;
+                else return false;
+            }
+        }
+        id = next_id++;
+        live.push_back({id, off, n, false});
+        head = off + n;
+        return true;
+    }
+    void release(uint64_t id) {
+        for (auto& b : live)
+            if (b.id == id) {
+                b.released = true;
+                break;
+            }
+        while (!live.empty() && live.front().released) live.pop_front();
+        if (live.empty()) head = 0;
+    }
+};
+
+struct OutBlock {
+    uint64_t ring_id = 0;
+    int64_t events = 0, cap = 0;
+    int refs = 0;
+    int32_t *ev_off, *status, *n_long, *hits, *vidx;
+    float *params, *state, *chi2;
+    int8_t* n;
+};
 
 struct Request {
     uint64_t id = 0;
     int64_t n_events = 0, n_hits = 0, n_velo = 0;
-    std::vector<int64_t> ev_off, velo_off;
-    std::vector<float> x, velo;
-    std::vector<int32_t> zone;
-    // results
-    std::vector<int32_t> s_ev_off, s_hits, s_status, l_vidx, l_nlong;
-    std::vector<float> s_params, s_state, l_chi2;
-    std::vector<int8_t> s_n;
+    size_t h_off = 0, v_off = 0;           // offsets in the hit / VELO rings
+    uint64_t h_id = 0, v_id = 0;           // ring blocks
+    std::vector<int64_t> ev_off, velo_off;  // rebased to 0
+    std::shared_ptr<OutBlock> out;         // results
+    int64_t e0 = 0, s0 = 0, s1 = 0;
     int status = ST_PENDING;
     bool done = false;
     int64_t t_submit = 0, t_launch = 0, t_done = 0;
@@ -846,23 +914,12 @@ struct Request {
 struct Slot {
     Workspace ws;
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev_counts = nullptr, ev_done = nullptr;
-    int64_t cap_events = 0, cap_hits = 0, cap_velo = 0, cap_seeds = 0;
-    // device buffers
+    cudaEvent_t ev = nullptr;
     int64_t *d_ev_off = nullptr, *d_velo_off = nullptr;
-    float *d_x = nullptr, *d_velo = nullptr;
-    int32_t* d_zone = nullptr;
-    int32_t *d_s_ev_off = nullptr, *d_s_hits = nullptr, *d_s_status = nullptr, *d_vidx = nullptr, *d_nlong = nullptr;
-    float *d_s_params = nullptr, *d_s_state = nullptr, *d_chi2 = nullptr;
-    int8_t* d_s_n = nullptr;
-    // pinned host staging
-    int64_t *h_ev_off = nullptr, *h_velo_off = nullptr;
-    float *h_x = nullptr, *h_velo = nullptr;
-    int32_t* h_zone = nullptr;
-    int32_t *h_s_ev_off = nullptr, *h_s_hits = nullptr, *h_s_status = nullptr, *h_vidx = nullptr, *h_nlong = nullptr;
-    float *h_s_params = nullptr, *h_s_state = nullptr, *h_chi2 = nullptr;
-    int8_t* h_s_n = nullptr;
+    int64_t *h_ev_off = nullptr, *h_velo_off = nullptr;  // pinned
+    int32_t* h_counts = nullptr;                          // pinned: the launch's seed offsets
     std::vector<std::shared_ptr<Request>> reqs;
+    std::shared_ptr<OutBlock> out;
     int64_t n_events = 0;
     bool busy = false;
     int rc = ST_OK;
@@ -871,15 +928,21 @@ struct Slot {
 struct Pipeline {
     st_pipeline_config pc;
     std::vector<Slot> slots;
+    Ring hr, vr, orr;  // hits, VELO states, outputs (bytes)
+    float* d_x = nullptr;
+    int32_t* d_zone = nullptr;
+    float* d_velo = nullptr;
+    char* d_out = nullptr;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done, cv_slot;
+    std::condition_variable cv_work, cv_done, cv_space;
     std::deque<std::shared_ptr<Request>> pending;
-    std::deque<int> launched;  // slot indices in launch order
+    std::deque<int> launched;
     std::map<uint64_t, std::shared_ptr<Request>> all;
     uint64_t next_id = 1;
     bool stop = false;
     std::thread dispatcher, completer;
-    std::string err;
+    std::mutex in_mu, out_mu;  // serialise use of the two DMA streams
+    cudaStream_t in_stream = nullptr, out_stream = nullptr;
 };
 
 extern "C" void st_pipeline_config_default(st_pipeline_config* pc) {
@@ -893,68 +956,52 @@ extern "C" void st_pipeline_config_default(st_pipeline_config* pc) {
     pc->max_velo_per_slot = 1ll << 20;
 }
 
-static size_t slot_device_bytes(st_ctx* ctx, const st_pipeline_config& pc, int64_t seeds_cap) {
-    Workspace t;
-    size_t b = carve(ctx, t, pc.max_events_per_slot, pc.max_hits_per_slot, pc.max_hits_per_event, seeds_cap, nullptr);
-    const int64_t E = pc.max_events_per_slot, Hh = pc.max_hits_per_slot;
-    const int64_t Vv = pc.max_velo_per_slot;
-    b += 2 * 8 * size_t(E + 1) + 8 * size_t(Hh) + 16 * size_t(Vv);
-    b += size_t(seeds_cap) * (48 + 32 + 16 + 2 + 8) + 12 * size_t(E + 1);
-    return b;
+static int64_t out_cap_for(int64_t hits) { return std::max<int64_t>(1024, hits / 8); }
+
+static size_t out_block_bytes(int64_t events, int64_t cap) {
+    return al256(4 * size_t(events + 1)) + 2 * al256(4 * size_t(events)) + al256(48 * size_t(cap)) +
+           al256(32 * size_t(cap)) + al256(16 * size_t(cap)) + al256(2 * size_t(cap)) + 2 * al256(4 * size_t(cap));
+}
+
+static void carve_out(OutBlock& o, char* p) {
+    size_t k = 0;
+    auto take = [&](size_t b) {
+        char* r = p + k;
+        k += al256(b);
+        return r;
+    };
+    o.ev_off = reinterpret_cast<int32_t*>(take(4 * size_t(o.events + 1)));
+    o.status = reinterpret_cast<int32_t*>(take(4 * size_t(o.events)));
+    o.n_long = reinterpret_cast<int32_t*>(take(4 * size_t(o.events)));
+    o.hits = reinterpret_cast<int32_t*>(take(48 * size_t(o.cap)));
+    o.params = reinterpret_cast<float*>(take(32 * size_t(o.cap)));
+    o.state = reinterpret_cast<float*>(take(16 * size_t(o.cap)));
+    o.n = reinterpret_cast<int8_t*>(take(2 * size_t(o.cap)));
+    o.vidx = reinterpret_cast<int32_t*>(take(4 * size_t(o.cap)));
+    o.chi2 = reinterpret_cast<float*>(take(4 * size_t(o.cap)));
 }
 
 static int slot_alloc(st_ctx* ctx, Slot& S, const st_pipeline_config& pc) {
-    S.cap_events = pc.max_events_per_slot;
-    S.cap_hits = pc.max_hits_per_slot;
-    S.cap_velo = pc.max_velo_per_slot;
-    S.cap_seeds = std::max<int64_t>(1024, S.cap_hits / 8);
     ST_CUDA(ctx, cudaStreamCreateWithFlags(&S.stream, cudaStreamNonBlocking));
-    ST_CUDA(ctx, cudaEventCreateWithFlags(&S.ev_counts, cudaEventDisableTiming));
-    ST_CUDA(ctx, cudaEventCreateWithFlags(&S.ev_done, cudaEventDisableTiming));
-    const int64_t E = S.cap_events, Hh = S.cap_hits, Vv = S.cap_velo, Sc = S.cap_seeds;
+    ST_CUDA(ctx, cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming));
+    const int64_t E = pc.max_events_per_slot;
     ST_CUDA(ctx, cudaMalloc(&S.d_ev_off, 8 * (E + 1)));
     ST_CUDA(ctx, cudaMalloc(&S.d_velo_off, 8 * (E + 1)));
-    ST_CUDA(ctx, cudaMalloc(&S.d_x, 4 * Hh));
-    ST_CUDA(ctx, cudaMalloc(&S.d_zone, 4 * Hh));
-    ST_CUDA(ctx, cudaMalloc(&S.d_velo, 16 * Vv));
-    ST_CUDA(ctx, cudaMalloc(&S.d_s_ev_off, 4 * (E + 1)));
-    ST_CUDA(ctx, cudaMalloc(&S.d_s_status, 4 * E));
-    ST_CUDA(ctx, cudaMalloc(&S.d_nlong, 4 * E));
-    ST_CUDA(ctx, cudaMalloc(&S.d_s_hits, 48 * Sc));
-    ST_CUDA(ctx, cudaMalloc(&S.d_s_params, 32 * Sc));
-    ST_CUDA(ctx, cudaMalloc(&S.d_s_state, 16 * Sc));
-    ST_CUDA(ctx, cudaMalloc(&S.d_s_n, 2 * Sc));
-    ST_CUDA(ctx, cudaMalloc(&S.d_vidx, 4 * Sc));
-    ST_CUDA(ctx, cudaMalloc(&S.d_chi2, 4 * Sc));
     ST_CUDA(ctx, cudaMallocHost(&S.h_ev_off, 8 * (E + 1)));
     ST_CUDA(ctx, cudaMallocHost(&S.h_velo_off, 8 * (E + 1)));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_x, 4 * Hh));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_zone, 4 * Hh));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_velo, 16 * Vv));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_s_ev_off, 4 * (E + 1)));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_s_status, 4 * E));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_nlong, 4 * E));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_s_hits, 48 * Sc));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_s_params, 32 * Sc));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_s_state, 16 * Sc));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_s_n, 2 * Sc));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_vidx, 4 * Sc));
-    ST_CUDA(ctx, cudaMallocHost(&S.h_chi2, 4 * Sc));
-    return ensure(ctx, S.ws, E, Hh, pc.max_hits_per_event, Sc, true);
+    ST_CUDA(ctx, cudaMallocHost(&S.h_counts, 4 * (E + 1)));
+    return ensure(ctx, S.ws, E, pc.max_hits_per_slot, pc.max_hits_per_event, out_cap_for(pc.max_hits_per_slot), true);
 }
 
 static void slot_free(Slot& S) {
     if (S.stream) cudaStreamSynchronize(S.stream);
-    void* dev[] = {S.d_ev_off, S.d_velo_off, S.d_x, S.d_zone, S.d_velo, S.d_s_ev_off, S.d_s_status, S.d_nlong,
-                   S.d_s_hits, S.d_s_params, S.d_s_state, S.d_s_n, S.d_vidx, S.d_chi2, S.ws.base};
-    for (void* p : dev)
-        if (p) cudaFree(p);
-    void* host[] = {S.h_ev_off, S.h_velo_off, S.h_x, S.h_zone, S.h_velo, S.h_s_ev_off, S.h_s_status, S.h_nlong,
-                    S.h_s_hits, S.h_s_params, S.h_s_state, S.h_s_n, S.h_vidx, S.h_chi2};
-    for (void* p : host)
-        if (p) cudaFreeHost(p);
-    if (S.ev_counts) cudaEventDestroy(S.ev_counts);
-    if (S.ev_done) cudaEventDestroy(S.ev_done);
+    if (S.d_ev_off) cudaFree(S.d_ev_off);
+    if (S.d_velo_off) cudaFree(S.d_velo_off);
+    if (S.ws.base) cudaFree(S.ws.base);
+    if (S.h_ev_off) cudaFreeHost(S.h_ev_off);
+    if (S.h_velo_off) cudaFreeHost(S.h_velo_off);
+    if (S.h_counts) cudaFreeHost(S.h_counts);
+    if (S.ev) cudaEventDestroy(S.ev);
     if (S.stream) cudaStreamDestroy(S.stream);
 }
 
@@ -963,58 +1010,71 @@ static void launch_slot(st_ctx* ctx, Pipeline& pl, int si, std::unique_lock<std:
     Slot& S = pl.slots[si];
     S.reqs.clear();
     int64_t ne = 0, nh = 0, nv = 0;
+    size_t next_h = 0, next_v = 0;
     while (!pl.pending.empty()) {
         auto& r = pl.pending.front();
-        if (!S.reqs.empty() && (ne + r->n_events > S.cap_events || nh + r->n_hits > S.cap_hits ||
-                                nv + r->n_velo > S.cap_velo))
-            break;
+        if (!S.reqs.empty()) {
+            // only a request that continues the previous one in both rings
+            // extends the launch's CSR without gaps
+            const bool contiguous = r->h_off == next_h && r->v_off == next_v;
+            if (!contiguous || ne + r->n_events > pl.pc.max_events_per_slot ||
+                nh + r->n_hits > pl.pc.max_hits_per_slot || nv + r->n_velo > pl.pc.max_velo_per_slot)
+                break;
+        }
         ne += r->n_events;
         nh += r->n_hits;
         nv += r->n_velo;
+        next_h = r->h_off + size_t(r->n_hits);
+        next_v = r->v_off + size_t(r->n_velo);
         S.reqs.push_back(r);
         pl.pending.pop_front();
     }
+    auto ob = std::make_shared<OutBlock>();
+    ob->events = ne;
+    ob->cap = out_cap_for(std::max<int64_t>(nh, 1));
+    size_t ob_off = 0;
+    while (!pl.stop && !pl.orr.alloc(out_block_bytes(ne, ob->cap), ob_off, ob->ring_id)) pl.cv_space.wait(lk);
+    if (pl.stop) {
+        for (auto it = S.reqs.rbegin(); it != S.reqs.rend(); ++it) pl.pending.push_front(*it);
+        S.reqs.clear();
+        return;
+    }
+    carve_out(*ob, pl.d_out + ob_off);
+    ob->refs = static_cast<int>(S.reqs.size());
+    S.out = ob;
     S.busy = true;
     S.n_events = ne;
     lk.unlock();
     const int64_t t0 = now_ns();
-    // concatenate into pinned staging
-    int64_t e = 0, h = 0, v = 0;
-    S.h_ev_off[0] = 0;
-    S.h_velo_off[0] = 0;
+    // the launch's CSR: absolute positions in the rings
+    int64_t e = 0;
+    S.h_ev_off[0] = int64_t(S.reqs.front()->h_off);
+    S.h_velo_off[0] = int64_t(S.reqs.front()->v_off);
     for (auto& r : S.reqs) {
         r->t_launch = t0;
-        std::memcpy(S.h_x + h, r->x.data(), 4 * r->n_hits);
-        std::memcpy(S.h_zone + h, r->zone.data(), 4 * r->n_hits);
-        std::memcpy(S.h_velo + 4 * v, r->velo.data(), 16 * r->n_velo);
+        r->e0 = e;
+        r->out = ob;
         for (int64_t k = 0; k < r->n_events; ++k) {
-            S.h_ev_off[e + k + 1] = h + r->ev_off[k + 1];
-            S.h_velo_off[e + k + 1] = v + r->velo_off[k + 1];
+            S.h_ev_off[e + k + 1] = int64_t(r->h_off) + r->ev_off[k + 1];
+            S.h_velo_off[e + k + 1] = int64_t(r->v_off) + r->velo_off[k + 1];
         }
         e += r->n_events;
-        h += r->n_hits;
-        v += r->n_velo;
     }
     cudaStream_t st = S.stream;
     int rc = ST_OK;
     auto ck = [&](cudaError_t err) {
         if (err != cudaSuccess && rc == ST_OK) rc = set_err(nullptr, ST_ECUDA, "%s", cudaGetErrorString(err));
     };
-    ck(cudaMemcpyAsync(S.d_ev_off, S.h_ev_off, 8 * (e + 1), cudaMemcpyHostToDevice, st));
-    ck(cudaMemcpyAsync(S.d_velo_off, S.h_velo_off, 8 * (e + 1), cudaMemcpyHostToDevice, st));
-    if (h) ck(cudaMemcpyAsync(S.d_x, S.h_x, 4 * h, cudaMemcpyHostToDevice, st));
-    if (h) ck(cudaMemcpyAsync(S.d_zone, S.h_zone, 4 * h, cudaMemcpyHostToDevice, st));
-    if (v) ck(cudaMemcpyAsync(S.d_velo, S.h_velo, 16 * v, cudaMemcpyHostToDevice, st));
-    st_hits H{e, S.d_ev_off, S.d_x, S.d_zone, nullptr, nullptr, pl.pc.max_hits_per_event, 0};
-    st_seeds Sd{S.cap_seeds, S.d_s_ev_off, S.d_s_hits, S.d_s_params, S.d_s_state, S.d_s_n, S.d_s_status};
-    st_velo V{e, S.d_velo_off, S.d_velo};
-    st_long L{S.d_vidx, S.d_chi2, S.d_nlong};
-    if (rc == ST_OK) rc = run_seeding(ctx, S.ws, H, Sd, st, S.cap_hits, false);
+    ck(cudaMemcpyAsync(S.d_ev_off, S.h_ev_off, 8 * (ne + 1), cudaMemcpyHostToDevice, st));
+    ck(cudaMemcpyAsync(S.d_velo_off, S.h_velo_off, 8 * (ne + 1), cudaMemcpyHostToDevice, st));
+    st_hits H{ne, S.d_ev_off, pl.d_x, pl.d_zone, nullptr, nullptr, pl.pc.max_hits_per_event, 0};
+    st_seeds Sd{ob->cap, ob->ev_off, ob->hits, ob->params, ob->state, ob->n, ob->status};
+    st_velo V{ne, S.d_velo_off, pl.d_velo};
+    st_long L{ob->vidx, ob->chi2, ob->n_long};
+    if (rc == ST_OK) rc = run_seeding(ctx, S.ws, H, Sd, st, pl.pc.max_hits_per_slot, false);
     if (rc == ST_OK) rc = run_matching(ctx, S.ws, V, Sd, L, st);
-    ck(cudaMemcpyAsync(S.h_s_ev_off, S.d_s_ev_off, 4 * (e + 1), cudaMemcpyDeviceToHost, st));
-    ck(cudaMemcpyAsync(S.h_s_status, S.d_s_status, 4 * e, cudaMemcpyDeviceToHost, st));
-    ck(cudaMemcpyAsync(S.h_nlong, S.d_nlong, 4 * e, cudaMemcpyDeviceToHost, st));
-    ck(cudaEventRecord(S.ev_counts, st));
+    ck(cudaMemcpyAsync(S.h_counts, ob->ev_off, 4 * (ne + 1), cudaMemcpyDeviceToHost, st));
+    ck(cudaEventRecord(S.ev, st));
     S.rc = rc;
     lk.lock();
     pl.launched.push_back(si);
@@ -1039,8 +1099,7 @@ static void dispatcher_main(st_ctx* ctx, Pipeline* pl) {
                 si = static_cast<int>(k);
                 break;
             }
-        if (si < 0) continue;
-        launch_slot(ctx, *pl, si, lk);
+        if (si >= 0) launch_slot(ctx, *pl, si, lk);
     }
 }
 
@@ -1055,55 +1114,25 @@ static void completer_main(st_ctx* ctx, Pipeline* pl) {
         Slot& S = pl->slots[si];
         lk.unlock();
         int rc = S.rc;
-        if (cudaEventSynchronize(S.ev_counts) != cudaSuccess && rc == ST_OK) rc = ST_ECUDA;
-        const int64_t e = S.n_events;
-        const int64_t ns = rc == ST_OK ? S.h_s_ev_off[e] : 0;
-        if (ns > 0) {
-            cudaStream_t st = S.stream;
-            cudaMemcpyAsync(S.h_s_hits, S.d_s_hits, 48 * ns, cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(S.h_s_params, S.d_s_params, 32 * ns, cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(S.h_s_state, S.d_s_state, 16 * ns, cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(S.h_s_n, S.d_s_n, 2 * ns, cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(S.h_vidx, S.d_vidx, 4 * ns, cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(S.h_chi2, S.d_chi2, 4 * ns, cudaMemcpyDeviceToHost, st);
-            cudaEventRecord(S.ev_done, st);
-            if (cudaEventSynchronize(S.ev_done) != cudaSuccess && rc == ST_OK) rc = ST_ECUDA;
-        }
-        // split the results back into the requests
-        int64_t e0 = 0;
+        if (cudaEventSynchronize(S.ev) != cudaSuccess && rc == ST_OK) rc = ST_ECUDA;
         const int64_t tdone = now_ns();
-        for (auto& r : S.reqs) {
-            const int64_t n = r->n_events;
-            const int64_t s0 = rc == ST_OK ? S.h_s_ev_off[e0] : 0;
-            const int64_t s1 = rc == ST_OK ? S.h_s_ev_off[e0 + n] : 0;
-            r->s_ev_off.resize(n + 1);
-            for (int64_t k = 0; k <= n; ++k) r->s_ev_off[k] = rc == ST_OK ? S.h_s_ev_off[e0 + k] - int32_t(s0) : 0;
-            r->s_status.assign(S.h_s_status + e0, S.h_s_status + e0 + n);
-            r->l_nlong.assign(S.h_nlong + e0, S.h_nlong + e0 + n);
-            r->s_hits.assign(S.h_s_hits + 12 * s0, S.h_s_hits + 12 * s1);
-            r->s_params.assign(S.h_s_params + 8 * s0, S.h_s_params + 8 * s1);
-            r->s_state.assign(S.h_s_state + 4 * s0, S.h_s_state + 4 * s1);
-            r->s_n.assign(S.h_s_n + 2 * s0, S.h_s_n + 2 * s1);
-            r->l_vidx.assign(S.h_vidx + s0, S.h_vidx + s1);
-            r->l_chi2.assign(S.h_chi2 + s0, S.h_chi2 + s1);
-            r->x.clear();
-            r->x.shrink_to_fit();
-            r->zone.clear();
-            r->zone.shrink_to_fit();
-            r->velo.clear();
-            r->velo.shrink_to_fit();
-            r->t_done = tdone;
-            e0 += n;
-        }
         lk.lock();
         for (auto& r : S.reqs) {
+            r->s0 = rc == ST_OK ? S.h_counts[r->e0] : 0;
+            r->s1 = rc == ST_OK ? S.h_counts[r->e0 + r->n_events] : 0;
+            r->t_done = tdone;
             r->status = rc;
             r->done = true;
+            // the inputs are no longer needed
+            pl->hr.release(r->h_id);
+            pl->vr.release(r->v_id);
         }
         S.reqs.clear();
+        S.out.reset();
         S.busy = false;
         pl->cv_done.notify_all();
         pl->cv_work.notify_all();
+        pl->cv_space.notify_all();
     }
 }
 
@@ -1123,6 +1152,17 @@ extern "C" int st_pipeline_configure(st_ctx* ctx, const st_pipeline_config* pcin
     return pipeline_configure_locked(ctx, pcin);
 }
 
+static void pipeline_free(Pipeline* pl) {
+    for (auto& S : pl->slots) slot_free(S);
+    if (pl->d_x) cudaFree(pl->d_x);
+    if (pl->d_zone) cudaFree(pl->d_zone);
+    if (pl->d_velo) cudaFree(pl->d_velo);
+    if (pl->d_out) cudaFree(pl->d_out);
+    if (pl->in_stream) cudaStreamDestroy(pl->in_stream);
+    if (pl->out_stream) cudaStreamDestroy(pl->out_stream);
+    delete pl;
+}
+
 static int pipeline_configure_locked(st_ctx* ctx, const st_pipeline_config* pcin) {
     if (ctx->pipe) return set_err(ctx, ST_ESTATE, "pipeline already configured");
     st_pipeline_config pc = *pcin;
@@ -1131,21 +1171,40 @@ static int pipeline_configure_locked(st_ctx* ctx, const st_pipeline_config* pcin
         pc.max_velo_per_slot < 1)
         return set_err(ctx, ST_EINVAL, "bad pipeline config");
     ST_CUDA(ctx, cudaSetDevice(ctx->device));
-    const int64_t seeds_cap = std::max<int64_t>(1024, pc.max_hits_per_slot / 8);
-    // device buffers and workspace, plus the pinned staging of the same size
-    const size_t per_slot = slot_device_bytes(ctx, pc, seeds_cap) + size_t(pc.max_hits_per_slot) * 8 +
-                            size_t(pc.max_velo_per_slot) * 16 + size_t(seeds_cap) * 110;
+    // device memory: per slot a workspace; shared input rings holding two
+    // slots' worth of hits and VELO states per slot; an output ring holding
+    // two launches' worth of results per slot
+    Workspace t;
+    const int64_t ocap = out_cap_for(pc.max_hits_per_slot);
+    const size_t ws_bytes = carve(ctx, t, pc.max_events_per_slot, pc.max_hits_per_slot, pc.max_hits_per_event,
+                                  ocap, nullptr);
+    const size_t in_bytes = 2 * (8 * size_t(pc.max_hits_per_slot) + 16 * size_t(pc.max_velo_per_slot));
+    const size_t out_bytes = 2 * out_block_bytes(pc.max_events_per_slot, ocap);
+    const size_t per_slot = ws_bytes + in_bytes + out_bytes;
     const int64_t fit = pc.mem_cap_bytes / int64_t(per_slot);
     if (fit < 1) return set_err(ctx, ST_ENOMEM, "one pipeline slot (%zu bytes) exceeds mem_cap_bytes", per_slot);
     pc.n_slots = static_cast<int32_t>(std::min<int64_t>(pc.n_slots, fit));
     Pipeline* pl = new Pipeline();
     pl->pc = pc;
+    pl->hr.cap = 2 * size_t(pc.max_hits_per_slot) * pc.n_slots;
+    pl->vr.cap = 2 * size_t(pc.max_velo_per_slot) * pc.n_slots;
+    pl->orr.cap = out_bytes * pc.n_slots;
+    cudaError_t e = cudaMalloc(&pl->d_x, 4 * pl->hr.cap);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_zone, 4 * pl->hr.cap);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_velo, 16 * pl->vr.cap);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_out, pl->orr.cap);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->in_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->out_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        pipeline_free(pl);
+        return set_err(ctx, e == cudaErrorMemoryAllocation ? ST_ENOMEM : ST_ECUDA, "pipeline memory: %s",
+                       cudaGetErrorString(e));
+    }
     pl->slots.resize(pc.n_slots);
     for (auto& S : pl->slots) {
         int rc = slot_alloc(ctx, S, pc);
         if (rc != ST_OK) {
-            for (auto& T : pl->slots) slot_free(T);
-            delete pl;
+            pipeline_free(pl);
             return rc;
         }
     }
@@ -1170,11 +1229,11 @@ static void pipeline_shutdown(st_ctx* ctx) {
         pl->stop = true;
         pl->cv_work.notify_all();
         pl->cv_done.notify_all();
+        pl->cv_space.notify_all();
     }
     pl->dispatcher.join();
     pl->completer.join();
-    for (auto& S : pl->slots) slot_free(S);
-    delete pl;
+    pipeline_free(pl);
     ctx->pipe = nullptr;
 }
 
@@ -1186,8 +1245,8 @@ extern "C" int pipeline_submit(st_ctx* ctx, const st_hits* hh, const st_velo* hv
     }
     Pipeline& pl = *ctx->pipe;
     const int64_t n = hh->n_events;
-    if (n < 1 || hv->n_events != n || !hh->ev_off || !hv->ev_off || (hh->ev_off[n] > hh->ev_off[0] && (!hh->x || !hh->zone)) ||
-        (hv->ev_off[n] > hv->ev_off[0] && !hv->state))
+    if (n < 1 || hv->n_events != n || !hh->ev_off || !hv->ev_off ||
+        (hh->ev_off[n] > hh->ev_off[0] && (!hh->x || !hh->zone)) || (hv->ev_off[n] > hv->ev_off[0] && !hv->state))
         return set_err(ctx, ST_EINVAL, "pipeline_submit: bad batch");
     auto r = std::make_shared<Request>();
     r->t_submit = now_ns();
@@ -1201,8 +1260,7 @@ extern "C" int pipeline_submit(st_ctx* ctx, const st_hits* hh, const st_velo* hv
         if (dh > pl.pc.max_hits_per_event || dv > pl.pc.max_velo_per_event)
             return set_err(ctx, ST_OVERFLOW, "pipeline_submit: event larger than the pipeline limits");
     }
-    Slot& S0 = pl.slots[0];
-    if (n > S0.cap_events || r->n_hits > S0.cap_hits || r->n_velo > S0.cap_velo)
+    if (n > pl.pc.max_events_per_slot || r->n_hits > pl.pc.max_hits_per_slot || r->n_velo > pl.pc.max_velo_per_slot)
         return set_err(ctx, ST_OVERFLOW, "pipeline_submit: batch larger than a pipeline slot");
     r->ev_off.resize(n + 1);
     r->velo_off.resize(n + 1);
@@ -1210,11 +1268,53 @@ extern "C" int pipeline_submit(st_ctx* ctx, const st_hits* hh, const st_velo* hv
         r->ev_off[k] = hh->ev_off[k] - h0;
         r->velo_off[k] = hv->ev_off[k] - v0;
     }
-    r->x.assign(hh->x + h0, hh->x + h0 + r->n_hits);
-    r->zone.assign(hh->zone + h0, hh->zone + h0 + r->n_hits);
-    r->velo.assign(hv->state + 4 * v0, hv->state + 4 * (v0 + r->n_velo));
+    {
+        // admission: wait (bounded) until the input rings have room
+        std::unique_lock<std::mutex> lk(pl.mu);
+        const auto deadline = std::chrono::steady_clock::now() + std::chrono::seconds(60);
+        for (;;) {
+            if (pl.stop) return set_err(ctx, ST_ESTATE, "pipeline stopping");
+            size_t ho, vo;
+            uint64_t hid, vid;
+            if (pl.hr.alloc(size_t(r->n_hits), ho, hid)) {
+                if (pl.vr.alloc(size_t(r->n_velo), vo, vid)) {
+                    r->h_off = ho;
+                    r->h_id = hid;
+                    r->v_off = vo;
+                    r->v_id = vid;
+                    break;
+                }
+                pl.hr.release(hid);
+            }
+            if (pl.cv_space.wait_until(lk, deadline) == std::cv_status::timeout)
+                return set_err(ctx, ST_TIMEOUT, "pipeline_submit: no room in the input rings for 60 s");
+        }
+    }
+    {
+        // DMA straight from the caller's memory; the caller may reuse its
+        // buffers when this returns
+        std::lock_guard<std::mutex> g(pl.in_mu);
+        cudaError_t e = cudaSuccess;
+        if (r->n_hits) {
+            e = cudaMemcpyAsync(pl.d_x + r->h_off, hh->x + h0, 4 * size_t(r->n_hits), cudaMemcpyHostToDevice,
+                                pl.in_stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(pl.d_zone + r->h_off, hh->zone + h0, 4 * size_t(r->n_hits),
+                                    cudaMemcpyHostToDevice, pl.in_stream);
+        }
+        if (e == cudaSuccess && r->n_velo)
+            e = cudaMemcpyAsync(pl.d_velo + 4 * r->v_off, hv->state + 4 * v0, 16 * size_t(r->n_velo),
+                                cudaMemcpyHostToDevice, pl.in_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(pl.in_stream);
+        if (e != cudaSuccess) {
+            std::lock_guard<std::mutex> g2(pl.mu);
+            pl.hr.release(r->h_id);
+            pl.vr.release(r->v_id);
+            pl.cv_space.notify_all();
+            return set_err(ctx, ST_ECUDA, "pipeline_submit: copy: %s", cudaGetErrorString(e));
+        }
+    }
     std::lock_guard<std::mutex> g(pl.mu);
-    if (pl.stop) return set_err(ctx, ST_ESTATE, "pipeline stopping");
     r->id = pl.next_id++;
     pl.all[r->id] = r;
     pl.pending.push_back(r);
@@ -1241,34 +1341,63 @@ extern "C" int pipeline_poll(st_ctx* ctx, uint64_t ticket, st_seeds* hs, st_long
             return ST_TIMEOUT;
         }
     }
-    if (r->status != ST_OK) {
+    auto finish = [&](std::unique_lock<std::mutex>& l) {
         pl.all.erase(ticket);
+        if (r->out && --r->out->refs == 0) {
+            pl.orr.release(r->out->ring_id);
+            pl.cv_space.notify_all();
+        }
+        r->out.reset();
+        (void)l;
+    };
+    if (r->status != ST_OK) {
+        finish(lk);
         return set_err(ctx, r->status, "pipeline batch failed");
     }
-    const int64_t ns = r->s_ev_off.empty() ? 0 : r->s_ev_off.back();
+    const int64_t n = r->n_events, ns = r->s1 - r->s0;
     if (!hs || !hs->ev_off || !hs->status || (ns > 0 && (!hs->hits || !hs->params || !hs->state || !hs->n_hits)))
         return set_err(ctx, ST_EINVAL, "pipeline_poll: null output");
-    if (hs->cap < ns) return set_err(ctx, ST_OVERFLOW, "pipeline_poll: host_seeds cap %lld < %lld", (long long)hs->cap, (long long)ns);
-    std::memcpy(hs->ev_off, r->s_ev_off.data(), 4 * r->s_ev_off.size());
-    std::memcpy(hs->status, r->s_status.data(), 4 * r->s_status.size());
-    if (ns > 0) {
-        std::memcpy(hs->hits, r->s_hits.data(), 4 * r->s_hits.size());
-        std::memcpy(hs->params, r->s_params.data(), 4 * r->s_params.size());
-        std::memcpy(hs->state, r->s_state.data(), 4 * r->s_state.size());
-        std::memcpy(hs->n_hits, r->s_n.data(), r->s_n.size());
+    if (hs->cap < ns)
+        return set_err(ctx, ST_OVERFLOW, "pipeline_poll: host_seeds cap %lld < %lld", (long long)hs->cap, (long long)ns);
+    std::shared_ptr<OutBlock> ob = r->out;
+    lk.unlock();
+    cudaError_t e = cudaSuccess;
+    {
+        // DMA straight into the caller's memory
+        std::lock_guard<std::mutex> g(pl.out_mu);
+        cudaStream_t st = pl.out_stream;
+        auto cp = [&](void* dst, const void* src, size_t bytes) {
+            if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+        };
+        const int64_t s0 = r->s0;
+        cp(hs->ev_off, ob->ev_off + r->e0, 4 * size_t(n + 1));
+        cp(hs->status, ob->status + r->e0, 4 * size_t(n));
+        cp(hs->hits, ob->hits + 12 * s0, 48 * size_t(ns));
+        cp(hs->params, ob->params + 8 * s0, 32 * size_t(ns));
+        cp(hs->state, ob->state + 4 * s0, 16 * size_t(ns));
+        cp(hs->n_hits, ob->n + 2 * s0, 2 * size_t(ns));
+        if (hl) {
+            if (hl->velo_idx) cp(hl->velo_idx, ob->vidx + s0, 4 * size_t(ns));
+            if (hl->chi2) cp(hl->chi2, ob->chi2 + s0, 4 * size_t(ns));
+            if (hl->n_long) cp(hl->n_long, ob->n_long + r->e0, 4 * size_t(n));
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    if (hl) {
-        if (ns > 0 && hl->velo_idx) std::memcpy(hl->velo_idx, r->l_vidx.data(), 4 * ns);
-        if (ns > 0 && hl->chi2) std::memcpy(hl->chi2, r->l_chi2.data(), 4 * ns);
-        if (hl->n_long) std::memcpy(hl->n_long, r->l_nlong.data(), 4 * r->l_nlong.size());
+    if (e == cudaSuccess) {
+        const int32_t base = hs->ev_off[0];
+        for (int64_t k = 0; k <= n; ++k) hs->ev_off[k] -= base;
     }
+    const int64_t tret = now_ns();
+    lk.lock();
+    finish(lk);
+    if (e != cudaSuccess) return set_err(ctx, ST_ECUDA, "pipeline_poll: copy: %s", cudaGetErrorString(e));
     if (info) {
         info->t_submit_ns = r->t_submit;
         info->t_launch_ns = r->t_launch;
         info->t_done_ns = r->t_done;
-        info->n_events = static_cast<int32_t>(r->n_events);
+        info->t_returned_ns = tret;
+        info->n_events = static_cast<int32_t>(n);
         info->n_seeds = static_cast<int32_t>(ns);
     }
-    pl.all.erase(ticket);
     return ST_OK;
 }

@@ -77,7 +77,7 @@ class StPipelineConfig(C.Structure):
 
 class StRequestInfo(C.Structure):
     _fields_ = [("t_submit_ns", C.c_int64), ("t_launch_ns", C.c_int64), ("t_done_ns", C.c_int64),
-                ("n_events", C.c_int32), ("n_seeds", C.c_int32)]
+                ("t_returned_ns", C.c_int64), ("n_events", C.c_int32), ("n_seeds", C.c_int32)]
 
 
 ST_OK, ST_PENDING, ST_EINVAL, ST_ENOMEM, ST_OVERFLOW, ST_TIMEOUT, ST_ECUDA, ST_ESTATE = 0, 1, -1, -2, -3, -4, -5, -6

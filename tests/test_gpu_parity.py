@@ -310,7 +310,105 @@ def test_pipeline_alone_and_in_the_mix(zmx):
         got = hb.to_numpy()
         for k in ("ev_off", "hits", "params", "state", "n_hits", "status", "velo_idx", "chi2", "n_long"):
             assert np.array_equal(got[k], alone[i][k]), (i, k)
-        assert info.n_events == n_ev and info.t_done_ns >= info.t_launch_ns >= info.t_submit_ns
+        assert info.n_events == n_ev and info.t_returned_ns >= info.t_done_ns >= info.t_launch_ns >= info.t_submit_ns
     # unknown ticket, and a poll that times out on nothing pending is an error
     assert ctx.lib.pipeline_poll(ctx.h, 123456789, None, None, 0, None) == st.ST_EINVAL
+    ctx.close()
+
+
+def _alone(ctx, b, a, c):
+    sub = b.subset(range(a, c))
+    out = st.run_batch(ctx, st.DeviceBatch.from_synth(sub, max_hits=8000))
+    torch.cuda.synchronize()
+    return out.to_numpy()
+
+
+def _poll_ok(ctx, t, n_ev):
+    hb = st.HostBuffers(n_ev, 300 * n_ev + 64)
+    rc, info = ctx.pipeline_poll(t, hb.seeds, hb.long, 60_000_000)
+    assert rc == st.ST_OK
+    return hb.to_numpy()
+
+
+def _same(got, want):
+    for k in ("ev_off", "hits", "params", "state", "n_hits", "status", "velo_idx", "chi2", "n_long"):
+        assert np.array_equal(got[k], want[k]), k
+
+
+def test_pipeline_ring_wraps(zmx):
+    """Small input rings (two slots' worth of hits) wrap many times while a
+    poller thread collects results; packing stops at every wrap."""
+    import threading
+    _, gcfg = parity.config_pair(zmx)
+    b = workload("run3", n_events=120)
+    rng = np.random.default_rng(21)
+    cuts = [0]
+    while cuts[-1] < b.n_events:
+        cuts.append(min(b.n_events, cuts[-1] + int(rng.integers(1, 8))))
+    ctx = st.Context(gcfg)
+    alone = [_alone(ctx, b, a, c) for a, c in zip(cuts[:-1], cuts[1:])]
+    ctx.st_pipeline_configure(n_slots=2, max_events_per_slot=16, max_hits_per_slot=20000,
+                              max_hits_per_event=8000, max_velo_per_event=1024, max_velo_per_slot=4000)
+    tickets = [None] * (len(cuts) - 1)
+    got = [None] * len(tickets)
+    err = []
+
+    def poller():
+        try:
+            for i in range(len(tickets)):
+                while tickets[i] is None:
+                    time.sleep(0.0005)
+                got[i] = _poll_ok(ctx, tickets[i], cuts[i + 1] - cuts[i])
+        except Exception as exc:
+            err.append(exc)
+
+    import time
+    th = threading.Thread(target=poller)
+    th.start()
+    keep = []
+    for i, (a, c) in enumerate(zip(cuts[:-1], cuts[1:])):
+        sub = b.subset(range(a, c))
+        hits, velo, k = st.HostBuffers.inputs(sub.ev_off, sub.x, sub.zone, sub.velo_off, sub.velo)
+        keep.append(k)
+        tickets[i] = ctx.pipeline_submit(hits, velo)
+    th.join(timeout=120)
+    assert not th.is_alive() and not err, err
+    for g, a in zip(got, alone):
+        _same(g, a)
+    ctx.close()
+
+
+def test_pipeline_threads_and_shuffled_polls(zmx):
+    """Four host threads submit concurrently; results are polled in a
+    shuffled order and each equals its batch run alone."""
+    import threading
+    _, gcfg = parity.config_pair(zmx)
+    b = workload("run3", n_events=160)
+    cuts = list(range(0, 161, 10))
+    ctx = st.Context(gcfg)
+    alone = [_alone(ctx, b, a, c) for a, c in zip(cuts[:-1], cuts[1:])]
+    ctx.st_pipeline_configure(n_slots=3, max_events_per_slot=64, max_hits_per_slot=64 * 4000,
+                              max_hits_per_event=8000, max_velo_per_event=1024)
+    tickets = [None] * len(alone)
+    errs = []
+
+    def submitter(idx):
+        try:
+            for i in idx:
+                sub = b.subset(range(cuts[i], cuts[i + 1]))
+                hits, velo, k = st.HostBuffers.inputs(sub.ev_off, sub.x, sub.zone, sub.velo_off, sub.velo)
+                tickets[i] = ctx.pipeline_submit(hits, velo)
+                del k
+        except Exception as exc:
+            errs.append(exc)
+
+    ths = [threading.Thread(target=submitter, args=(list(range(j, len(alone), 4)),)) for j in range(4)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join(timeout=120)
+    assert not errs, errs
+    order = np.random.default_rng(5).permutation(len(alone))
+    for i in order:
+        _same(_poll_ok(ctx, tickets[i], 10), alone[i])
     ctx.close()
