@@ -307,19 +307,16 @@ struct UV {
     float chi2, tyr, beta, wm, zm;
 };
 
-// One UV combination (Section 3.4): start from the kinit-th hit of the
-// initial stereo layer of `pass`, ty from the origin, closest hit within
-// uv_tol in each remaining stereo layer in increasing z with ty averaging,
-// then (fit = true, n >= n_uv_min) the straight-line fit y = y0 + ty z.  A
-// combination that can no longer reach n_uv_min stops early (its result is
-// unused either way).  The y of each hit is formed as a float-float from
-// error-free transformations and fitted relative to the line y = tyr z, so
-// chi2_y keeps ~1e-6 relative accuracy.
-__device__ void uv_combo(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
-                         const float* th, const float* dth, int pass, int kinit, bool fit, UV& o) {
+// The search chain of one UV combination (Section 3.4): start from the
+// kinit-th hit of the initial stereo layer of `pass`, ty from the origin,
+// closest hit within uv_tol in each remaining stereo layer in increasing z
+// with ty averaging.  Xs[u] is the seed's x at stereo slot u.  A chain that
+// can no longer reach n_uv_min stops early (it cannot be selected).
+__device__ void uv_chain(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
+                         const float* Xs, int pass, int kinit, UV& o) {
     const int ui = P.uv_init[pass];
     const int pi = szl[6 + ui] + kinit;
-    const float yi = (x_at_uv(P, th, dth, ui) - X[pi]) * P.uinv_t[ui];
+    const float yi = (Xs[ui] - X[pi]) * P.uinv_t[ui];
     float ty = yi * P.uinv_z[ui];
     int n = 1;
     o.n = 0;
@@ -330,7 +327,7 @@ __device__ void uv_combo(const DevParams& P, const float* X, const int* szl, con
             o.pos[u] = pi;
             continue;
         }
-        const float Xl = x_at_uv(P, th, dth, u);
+        const float Xl = Xs[u];
         const float xp = Xl - P.ut[u] * ty * P.uz[u];
         const int st = szl[6 + u], nn = szl[7 + u] - st;
         const float* xs = X + st;
@@ -359,14 +356,17 @@ __device__ void uv_combo(const DevParams& P, const float* X, const int* szl, con
         }
     }
     o.n = n;
-    o.chi2 = 0.f;
     o.tyr = ty;
-    o.beta = 0.f;
-    o.wm = 0.f;
-    o.zm = 0.f;
-    if (!fit || n < P.n_uv_min) return;
+}
+
+// Straight-line fit y = y0 + ty z of a complete chain (o.pos, o.n, o.tyr).
+// The y of each hit is formed as a float-float from error-free
+// transformations and fitted relative to the line y = tyr z, so chi2_y keeps
+// ~1e-6 relative accuracy.
+__device__ void uv_fit(const DevParams& P, const float* X, const float* th, const float* dth, UV& o) {
     float w[6];
     float sw = 0.f, sz = 0.f;
+    const float ty = o.tyr;
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
         w[u] = 0.f;
@@ -391,7 +391,7 @@ __device__ void uv_combo(const DevParams& P, const float* X, const int* szl, con
         sw += w[u];
         sz += P.uzt[u];
     }
-    const float inv_n = 1.f / static_cast<float>(n);
+    const float inv_n = 1.f / static_cast<float>(o.n);
     const float wm = sw * inv_n, zm = sz * inv_n;
     float szz = 0.f, szw = 0.f;
 #pragma unroll
@@ -415,9 +415,16 @@ __device__ void uv_combo(const DevParams& P, const float* X, const int* szl, con
     o.zm = zm;
 }
 
-__device__ __forceinline__ ull uv_key(int n, float chi2, int pass, int kinit) {
-    return (ull(6 - n) << 61) | (ull(__float_as_uint(chi2) & 0x7fffffffu) << 30) |
-           (ull(pass) << 29) | ull(kinit);
+// A selection key per UV combination: fewer missing hits, then smaller chi2_y,
+// then pass A, then the earlier initial hit (the order of Section 3.4's
+// choice); the lowest 13 bits carry where the combination's hits were stored
+// (kUvNotStored if they were not) and never decide.
+constexpr int kUvStore = 8191;
+constexpr int kUvNotStored = 8191;
+
+__device__ __forceinline__ ull uv_key(int n, float chi2, int pass, int kinit, int stored) {
+    return (ull(6 - n) << 61) | (ull(__float_as_uint(chi2) & 0x7fffffffu) << 30) | (ull(pass) << 29) |
+           (ull(kinit) << 13) | ull(stored);
 }
 
 __device__ __forceinline__ ull pack_trip(int it, int k1, int k3, int k2) {
@@ -447,12 +454,14 @@ constexpr int kTripPerCand = 2;  // triplet buffer entries per candidate slot
 
 size_t seed_smem_bytes(int threads, int smem_hits, int tbl_smem, int key_smem) {
     return align16(sizeof(float) * smem_hits) + align16(sizeof(uint16_t) * 12 * kLutBins) +
-           sizeof(ull) * (tbl_smem + key_smem) + sizeof(int) * 3 * threads + sizeof(int) * (36 + 16);
+           sizeof(ull) * (tbl_smem + key_smem) + sizeof(float) * 6 * key_smem + sizeof(int) * 3 * threads +
+           sizeof(int) * (36 + 16);
 }
 
 size_t seed_slot_bytes(int cand_cap, int max_xhits) {
     return align16(sizeof(int) * 16 * size_t(cand_cap)) +
-           sizeof(ull) * (size_t(max_xhits) + cand_cap + size_t(kTripPerCand) * cand_cap);
+           sizeof(ull) * (size_t(max_xhits) + cand_cap + size_t(kTripPerCand) * cand_cap) +
+           16 + sizeof(uint4) * kUvStore + sizeof(float) * 6 * size_t(cand_cap);
 }
 
 // two CTAs of 512 threads (four of 256) per SM: 64 registers per thread
@@ -469,6 +478,8 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     sp += sizeof(ull) * A.tbl_smem;
     ull* skey = reinterpret_cast<ull*>(sp);
     sp += sizeof(ull) * A.key_smem;
+    float* sXs = reinterpret_cast<float*>(sp);  // x at the 6 stereo layers per kept seed
+    sp += sizeof(float) * 6 * A.key_smem;
     int* sPS = reinterpret_cast<int*>(sp);
     int* sA = sPS + T;
     int* sB = sA + T;
@@ -487,6 +498,11 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     ull* g_tbl = reinterpret_cast<ull*>(slot + align16(sizeof(int) * 16 * size_t(CC)));
     ull* g_key = g_tbl + A.max_xhits;
     ull* trip = g_key + CC;
+    // hits + ty of stored UV chains (16-byte aligned: the clone table before it
+    // has max_xhits 8-byte entries, which may be odd)
+    uint4* vstore = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(trip + TC) + 15) & ~uintptr_t(15));
+    float* g_xs = reinterpret_cast<float*>(vstore + kUvStore);
+    __shared__ int s_nvalid;
 
     ull ctr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
@@ -692,18 +708,25 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
 
         // ------------------------------------------------------------ UV
         ull* ukey = nk <= A.key_smem ? skey : g_key;
-        for (int j = tid; j < nk; j += T) ukey[j] = ~0ull;
+        float* Xs = nk <= A.key_smem ? sXs : g_xs;
+        for (int j = tid; j < nk; j += T) {
+            ukey[j] = ~0ull;
+            const int k = kept[j];
+            const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
+            const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
+#pragma unroll
+            for (int u = 0; u < 6; ++u) Xs[6 * j + u] = x_at_uv(P, th, dth, u);
+        }
+        if (tid == 0) s_nvalid = 0;
         __syncthreads();
         const int nuv = 2 * nk;
         for (int b = 0; b < nuv; b += T) {
             const int i = b + tid;
             int cntc = 0, lo = 0;
             if (i < nuv) {
-                const int k = kept[i >> 1], pass = i & 1;
-                const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
-                const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
+                const int j = i >> 1, pass = i & 1;
                 const int ui = P.uv_init[pass];
-                const float Xi = x_at_uv(P, th, dth, ui);
+                const float Xi = Xs[6 * j + ui];
                 const float t = P.ut[ui];
                 const float xa = fmaf(-P.uv_yhi[h], t, Xi), xb = fmaf(-P.uv_ylo[h], t, Xi);
                 const int st = szl[6 + ui], n = szl[7 + ui] - st;
@@ -732,14 +755,26 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     }
                     const int it2 = sB[o];
                     const int j = it2 >> 1, pass = it2 & 1;
-                    const int k = kept[j];
-                    const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
-                    const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
                     UV u;
-                    uv_combo(P, X, szl, lut, th, dth, pass, kinit, true, u);
+                    uv_chain(P, X, szl, lut, Xs + 6 * j, pass, kinit, u);
                     if (u.n >= P.n_uv_min) {
                         ++ctr[6];
-                        atomicMin(&ukey[j], uv_key(u.n, u.chi2, pass, kinit));
+                        const int k = kept[j];
+                        const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
+                        const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
+                        uv_fit(P, X, th, dth, u);
+                        int sidx = atomicAdd(&s_nvalid, 1);
+                        if (sidx < kUvStore) {
+                            uint4 r;
+                            r.x = (unsigned(u.pos[0] + 1) & 0xFFFFu) | (unsigned(u.pos[1] + 1) << 16);
+                            r.y = (unsigned(u.pos[2] + 1) & 0xFFFFu) | (unsigned(u.pos[3] + 1) << 16);
+                            r.z = (unsigned(u.pos[4] + 1) & 0xFFFFu) | (unsigned(u.pos[5] + 1) << 16);
+                            r.w = __float_as_uint(u.tyr);
+                            vstore[sidx] = r;
+                        } else {
+                            sidx = kUvNotStored;
+                        }
+                        atomicMin(&ukey[j], uv_key(u.n, u.chi2, pass, kinit, sidx));
                     }
                     ++kinit;
                 }
@@ -779,20 +814,33 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             if (has) {
                 const int64_t r = int64_t(s_start) + wbase + o;
                 const ull key = ukey[j];
-                const int pass = static_cast<int>((key >> 29) & 1);
-                const int kinit = static_cast<int>(key & ((1u << 29) - 1));
+                const int sidx = static_cast<int>(key & 0x1FFFu);
                 const int k = kept[j];
                 const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
                 const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
                 UV u;
-                uv_combo(P, X, szl, lut, th, dth, pass, kinit, true, u);
+                if (sidx != kUvNotStored) {
+                    const uint4 v = vstore[sidx];
+                    const unsigned w[3] = {v.x, v.y, v.z};
+                    u.n = 0;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        u.pos[q] = static_cast<int>((w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu) - 1;
+                        u.n += u.pos[q] >= 0;
+                    }
+                    u.tyr = __uint_as_float(v.w);
+                } else {
+                    uv_chain(P, X, szl, lut, Xs + 6 * j, static_cast<int>((key >> 29) & 1),
+                             static_cast<int>((key >> 13) & 0xFFFFu), u);
+                }
+                uv_fit(P, X, th, dth, u);
                 int32_t* ho = A.pool_hits + r * 12;
 #pragma unroll
-                for (int s = 0; s < 6; ++s) {
-                    const int p = c_pos[s * CC + k];
-                    ho[kXLayer[s]] = p >= 0 ? A.corig[cbh + p] : -1;
-                    const int q = u.pos[s];
-                    ho[kULayer[s]] = q >= 0 ? A.corig[cbh + q] : -1;
+                for (int q = 0; q < 6; ++q) {
+                    const int p = c_pos[q * CC + k];
+                    ho[kXLayer[q]] = p >= 0 ? A.corig[cbh + p] : -1;
+                    const int qq = u.pos[q];
+                    ho[kULayer[q]] = qq >= 0 ? A.corig[cbh + qq] : -1;
                 }
                 const float a = th[0] + dth[0], bb = th[1] + dth[1], cc = th[2] + dth[2];
                 // y(z) = tyr z + wm + beta (z - zc - zm)
