@@ -216,7 +216,8 @@ struct Trip {
 // correction dth = G y and the chi2 are then computed from small numbers.
 // Returns 0 (fewer than 5 hits), 1 (chi2 cut) or 2 (candidate).
 __device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, const int* szl,
-                          const uint16_t* lut, int k1, int k2, int k3, Trip& o) {
+                          const uint16_t* lut, const float* sG, const int* sMask, int k1, int k2, int k3,
+                          Trip& o) {
     const int p1 = szl[I.s1] + k1, p2 = szl[I.s2] + k2, p3 = szl[I.s3] + k3;
     const float x1 = X[p1], x2 = X[p2], x3 = X[p3];
     const float t13 = (x3 - x1) * I.inv_dz31;
@@ -256,7 +257,7 @@ __device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, co
         m |= (p >= 0) << s;
     }
     if (nx < 5) return 0;
-    const int mi = P.mask_index[m];
+    const float* G = sG + 18 * sMask[m];  // [3][6] gain of this hit pattern
     float y[6];
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
@@ -272,9 +273,9 @@ __device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, co
     float da = 0.f, db = 0.f, dc = 0.f;
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
-        da = fmaf(P.G[mi][0][s], y[s], da);
-        db = fmaf(P.G[mi][1][s], y[s], db);
-        dc = fmaf(P.G[mi][2][s], y[s], dc);
+        da = fmaf(G[s], y[s], da);
+        db = fmaf(G[6 + s], y[s], db);
+        dc = fmaf(G[12 + s], y[s], dc);
     }
     float chi2 = 0.f;
 #pragma unroll
@@ -451,6 +452,7 @@ __device__ __forceinline__ int pair_window(const DevParams& P, const IterP& I, c
 }
 
 constexpr int kTripPerCand = 2;  // triplet buffer entries per candidate slot
+constexpr int kTripLocal = 8;    // triplets a thread buffers while walking its pairs
 
 size_t seed_smem_bytes(int threads, int smem_hits, int tbl_smem, int key_smem) {
     return align16(sizeof(float) * smem_hits) + align16(sizeof(uint16_t) * 12 * kLutBins) +
@@ -461,7 +463,8 @@ size_t seed_smem_bytes(int threads, int smem_hits, int tbl_smem, int key_smem) {
 size_t seed_slot_bytes(int cand_cap, int max_xhits) {
     return align16(sizeof(int) * 16 * size_t(cand_cap)) +
            sizeof(ull) * (size_t(max_xhits) + cand_cap + size_t(kTripPerCand) * cand_cap) +
-           16 + sizeof(uint4) * kUvStore + sizeof(float) * 6 * size_t(cand_cap);
+           16 + sizeof(uint4) * kUvStore + sizeof(float) * 6 * size_t(cand_cap) + 8 +
+           sizeof(ull) * kTripLocal * kMaxThreads;
 }
 
 // two CTAs of 512 threads (four of 256) per SM: 64 registers per thread
@@ -487,6 +490,12 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     int* szl = tmp + 36;
     __shared__ int s_item;
     __shared__ ull s_start;
+    // the x-z fit gains, indexed per thread by hit pattern: kept in shared
+    // memory (divergent reads of kernel parameters serialise)
+    __shared__ float sG[kMasks * 18];
+    __shared__ int sMask[64];
+    for (int i = tid; i < kMasks * 18; i += T) sG[i] = (&P.G[0][0][0])[i];
+    for (int i = tid; i < 64; i += T) sMask[i] = P.mask_index[i];
 
     const int CC = A.cand_cap;
     const int TC = kTripPerCand * CC;
@@ -502,6 +511,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     // has max_xhits 8-byte entries, which may be odd)
     uint4* vstore = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(trip + TC) + 15) & ~uintptr_t(15));
     float* g_xs = reinterpret_cast<float*>(vstore + kUvStore);
+    ull* tloc = reinterpret_cast<ull*>(g_xs + 6 * CC) + tid * kTripLocal;  // this thread's triplet buffer
     __shared__ int s_nvalid;
 
     ull ctr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -584,26 +594,18 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             int ntrip = 0;
             const int pb = static_cast<int>((int64_t(tot_p) * tid) / T);
             const int pe = static_cast<int>((int64_t(tot_p) * (tid + 1)) / T);
-            // walk [pb, pe): pass 0 counts, pass 1 writes
-            int nt = 0, wofs = 0;
-            for (int pass = 0; pass < 2; ++pass) {
-                if (pass == 1) {
-                    int tot_t;
-                    wofs = block_exscan(nt, tmp, tot_t);
-                    ctr[1] += nt;
-                    if (ntrip + tot_t > TC) overflow = true;
-                    if (overflow) break;
-                    wofs += ntrip;
-                    ntrip += tot_t;
-                }
-                if (pb >= pe) continue;
+            // walk [pb, pe) once, buffering up to kTripLocal triplets per
+            // thread; only if some thread found more is the walk repeated to
+            // write them in place
+            auto walk = [&](bool direct, int wofs) {
+                int w = 0;
+                if (pb >= pe) return 0;
                 int o = owner_of(sPS, T, pb);
                 int nxt = o + 1 < T ? sPS[o + 1] : tot_p;
                 int k3 = sA[o] + (pb - sPS[o]);
                 int tg = sB[o];
                 int it = tg >> 20, k1 = tg & 0xFFFFF;
                 float x1 = X[szl[P.it[it].s1] + k1];
-                int w = 0;
                 for (int p = pb; p < pe; ++p) {
                     while (p >= nxt) {
                         ++o;
@@ -617,12 +619,30 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     const IterP& I = P.it[it];
                     int lo2;
                     const int c = pair_window(P, I, X, szl, lut, x1, X[szl[I.s3] + k3], lo2);
-                    if (pass == 1)
-                        for (int q = 0; q < c; ++q) trip[wofs + w + q] = pack_trip(it, k1, k3, lo2 + q);
+                    for (int q = 0; q < c; ++q) {
+                        const ull key = pack_trip(it, k1, k3, lo2 + q);
+                        if (direct) trip[wofs + w + q] = key;
+                        else if (w + q < kTripLocal) tloc[w + q] = key;
+                    }
                     w += c;
                     ++k3;
                 }
-                if (pass == 0) nt = w;
+                return w;
+            };
+            const int nt = walk(false, 0);
+            const int again = __syncthreads_or(nt > kTripLocal);
+            int tot_t;
+            int wofs = block_exscan(nt, tmp, tot_t);
+            ctr[1] += nt;
+            if (ntrip + tot_t > TC) overflow = true;
+            if (!overflow) {
+                wofs += ntrip;
+                ntrip += tot_t;
+                if (again) {
+                    walk(true, wofs);
+                } else {
+                    for (int q = 0; q < nt; ++q) trip[wofs + q] = tloc[q];
+                }
             }
             __syncthreads();
             if (overflow) break;
@@ -635,7 +655,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 if (t < ntrip) {
                     const ull tk = trip[t];
                     const int it = static_cast<int>(tk >> 60);
-                    code = do_triplet(P, P.it[it], X, szl, lut, static_cast<int>((tk >> 40) & 0xFFFFF),
+                    code = do_triplet(P, P.it[it], X, szl, lut, sG, sMask, static_cast<int>((tk >> 40) & 0xFFFFF),
                                       static_cast<int>(tk & 0xFFFFF), static_cast<int>((tk >> 20) & 0xFFFFF), o);
                     ctr[2] += code >= 1;
                 }

@@ -139,7 +139,7 @@ extern "C" void st_config_default(st_config* c) {
     c->chi2_match_max = 2.0;
     c->velo_unique = 0;
     c->threads_seed = 256;
-    c->threads_build = 256;
+    c->threads_build = 512;
     c->threads_match = 256;
     c->ctas_per_sm = 0;
     c->smem_hits = 2048;
@@ -405,11 +405,13 @@ static void tmark(st_ctx* ctx, const Workspace& w, int k, int end, cudaStream_t 
 constexpr int kBuildSmemHits = 6144;  // larger events keep their per-hit arrays in scratch
 constexpr int kBuildCtasPerSm = 8;
 
-// buckets per container slot for a batch: about one hit per bucket
+// buckets per container slot for a batch: about four hits per bucket (the
+// rank sort inside a bucket is quadratic but tiny; fewer buckets mean less
+// to clear and scan per event)
 static int bins_for(int64_t n_events, int64_t n_hits) {
     const double avg = n_events > 0 ? double(n_hits) / double(n_events) : 0.0;
     int b = 8;
-    while (b < 512 && b * 24 < avg) b <<= 1;
+    while (b < 512 && b * 96 < avg) b <<= 1;
     return b;
 }
 

@@ -146,7 +146,7 @@ extern "C" int seeding_run_static(const st_config* cfg, const st_hits* H, st_see
     unsigned long long* counters = reinterpret_cast<unsigned long long*>(b + o_cnt);
 
     int bins = 8;
-    while (bins < 512 && bins * 24 < mh) bins <<= 1;
+    while (bins < 512 && bins * 96 < mh) bins <<= 1;
     const size_t bsmem = build_smem_bytes(bins, static_cast<int>(mh));
     const int bbps = std::max(1, build_blocks_per_sm(cfg->threads_build, bsmem));
     const int g_build = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ne, int64_t(D->n_sms) * bbps)));
