@@ -41,6 +41,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2606_14480_gb300.replicas import dist_env, job_rate, max_over_ranks, replica_seed  # noqa: E402
+
 WORKLOAD = "run3"
 METRIC = "events/s (Seeding+Matching) on 1 GB300, batched/served vs per-event launch; p99 latency"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
@@ -54,13 +56,6 @@ OPS_PER_UNIT = {"pairs": 12.0, "triplets": 40.0, "fits": 120.0, "uv_init": 60.0,
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
-
-
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
 
 
 def measured_peaks():
@@ -156,13 +151,14 @@ def traffic_from_profile(kernel):
 # oracle (CPU) timing
 # ---------------------------------------------------------------------------
 
-def time_oracle(batch, zmx, budget_s=12.0, events=None):
-    """Seeding + matching of events by the FP64 oracle on all host cores,
-    one event per task; stops after the budget.  Returns (events/s, cores, n)."""
+def time_oracle(batch, zmx, budget_s=12.0, events=None, cores=None):
+    """Seeding + matching of events by the FP64 oracle on `cores` host
+    threads (all by default), one event per task; stops after the budget.
+    Returns (events/s, cores, n)."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     cfg = oracle.default_config(zmx=zmx)
-    cores = os.cpu_count() or 1
+    cores = cores or os.cpu_count() or 1
     events = list(range(batch.n_events)) if events is None else list(events)
 
     def one(e):
@@ -230,6 +226,7 @@ def main():
     ap.add_argument("--per-event", type=int, default=200, help="events timed with per-event launches")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="batched measurement only (for profiling)")
+    ap.add_argument("--no-autotune", action="store_true", help="paper defaults, no launch-shape tuning")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -246,10 +243,32 @@ def main():
     from paper_2606_14480_gb300 import st
     from synth import calibrate_zmatch, make_workload
 
-    batch = make_workload(WORKLOAD, seed=1002 + rank)
+    batch = make_workload(WORKLOAD, seed=replica_seed(1002, rank))
     n_ev = batch.n_events
     zmx = calibrate_zmatch(7826.0)
-    cfg = st.st_config_default(zmx=zmx)
+
+    # ---------------- autotuner: launch shapes (result-invariant, applied) and
+    # window widths (truth-scored, reported; the paper's widths are kept)
+    tuned, tune_report = {}, None
+    if not args.no_autotune:
+        from paper_2606_14480_gb300 import autotune
+        t0 = time.perf_counter()
+        calib = autotune.calibration_from_synth(batch)
+        tb = autotune._Bench(calib, local, reps=5, flush_mb=256)
+        lr = autotune.tune_launch({"zmx": zmx}, bench=tb)
+        tuned = dict(lr.best)
+        tune_report = {"launch": lr.report(), "applied": tuned}
+        if not args.quick:
+            wr = autotune.tune_windows(dict({"zmx": zmx}, **tuned), bench=tb)
+            tune_report["windows"] = wr.report()
+            tune_report["windows"]["grid"] = [
+                {"overrides": q.overrides, "ms": q.ms, "eff": q.eff, "ghost": q.ghost, "ok": q.ok}
+                for q in wr.points]
+            tune_report["windows"]["applied"] = False
+        del tb
+        tune_report["seconds"] = time.perf_counter() - t0
+        log(f"autotune: {tune_report}")
+    cfg = st.st_config_default(zmx=zmx, **tuned)
     ctx = st.Context(cfg, device=local)
     db = st.DeviceBatch.from_synth(batch, device=dev)
     cap = max(1024, batch.n_hits // 4)
@@ -288,11 +307,8 @@ def main():
     counters = ctx.st_read_counters(reset=True)
     total_ms = float(np.sum(step_ms))
     log(f"batched: {np.mean(step_ms):.3f} ms/step, kernels {kms}")
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * n_ev * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(total_ms, device=dev)
+    value = job_rate(n_ev * args.steps, ws, total_ms / 1000.0)
     ms_per_step = total_ms / args.steps
 
     result = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": ws, "steps": args.steps,
@@ -307,6 +323,9 @@ def main():
               "gpu_launches": kernels_per_step * args.steps}
     if clk:
         result["clocks"] = clk
+    if tune_report is not None:
+        result["config"]["launch"] = {k: int(v) for k, v in tuned.items()}
+        result["autotune"] = tune_report
 
     # ---------------- roofline of the seeding kernel
     peaks, src = measured_peaks()
@@ -361,12 +380,9 @@ def main():
     ns = int(hb.ev_off[-1])
     d2h = 4 * (n_ev + 1) + 8 * n_ev + ns * (48 + 32 + 16 + 2 + 8)
     e2e_total = float(np.sum(e2e_t))
-    if ws > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, device=dev)
     log(f"e2e: {1000 * e2e_total / args.steps:.3f} ms/step")
-    result["e2e"] = {"value": ws * n_ev * args.steps / e2e_total, "unit": "events/s",
+    result["e2e"] = {"value": job_rate(n_ev * args.steps, ws, e2e_total), "unit": "events/s",
                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                      "api": "pipeline_submit + pipeline_poll, host buffers, one batch in flight"}
 
@@ -391,16 +407,20 @@ def main():
                 ctx3.matching_run(v, outs.seeds, outs.long, stream)
             stream.synchronize()
             structs = [ev_struct(e) for e in range(pe)]
-            ev0.record(stream)
-            for h, v in structs:
+            marks = [torch.cuda.Event(enable_timing=True) for _ in range(pe + 1)]
+            marks[0].record(stream)
+            for (h, v), m in zip(structs, marks[1:]):
                 ctx3.seeding_run(h, outs.seeds, stream)
                 ctx3.matching_run(v, outs.seeds, outs.long, stream)
-            ev1.record(stream)
-            ev1.synchronize()
-        pe_ms = ev0.elapsed_time(ev1)
+                m.record(stream)
+            marks[-1].synchronize()
+        pe_ms = marks[0].elapsed_time(marks[-1])
+        per = np.array([a.elapsed_time(b) for a, b in zip(marks, marks[1:])])
         result["per_event"] = {"value": pe / (pe_ms / 1000.0), "unit": "events/s", "events_timed": pe,
                                "launches_per_event": kernels_per_step,
-                               "mode": "seeding_run + matching_run per event, one stream"}
+                               "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+                               "mode": "seeding_run + matching_run per event, one stream (latency: between "
+                                       "consecutive events' completion on the stream)"}
         del C
         ctx3.close()
         log(f"per-event: {pe_ms / pe:.4f} ms/event")
@@ -411,10 +431,18 @@ def main():
 
         # ---------------- CPU baseline: the oracle on the host cores
         if not args.no_cpu_baseline:
-            v, cores, n = time_oracle(batch, zmx, budget_s=12.0)
+            v, cores, n = time_oracle(batch, zmx, budget_s=10.0)
+            v1, _, n1 = time_oracle(batch, zmx, budget_s=4.0, cores=1)
+            unev = make_workload("uneven", n_events=2000, seed=1003)
+            vu, _, nu = time_oracle(unev, zmx, budget_s=6.0)
+            vu1, _, nu1 = time_oracle(unev, zmx, budget_s=4.0, cores=1)
             result["cpu_baseline"] = {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
                                       "sample": f"{n} events of the workload (cycled), seeding + matching, "
-                                                f"FP64, one event per task on {cores} threads, ~12 s"}
+                                                f"FP64, one event per task on {cores} threads, ~10 s",
+                                      "one_core": {"value": v1, "events": n1},
+                                      "uneven": {"value": vu, "events": nu, "one_core": vu1, "one_core_events": nu1,
+                                                 "sample": "2000 events of the uneven-occupancy mix "
+                                                           "(log-normal, median 120 tracks), cycled"}}
     ctx2.close()
     graph.close()
     ctx.close()

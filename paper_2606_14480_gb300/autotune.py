@@ -1,0 +1,304 @@
+"""Autotuner for the seeding + matching chain on one GPU.
+
+Two searches run on one calibration batch kept resident on the device, each
+point timed as a replay of the chain's CUDA graph (container build, seeding,
+CSR gather, matching) with CUDA events, the L2 flushed before every replay:
+
+* Launch shapes -- threads per CTA of the build, seeding and matching kernels,
+  persistent CTAs per SM (how many (event, half) work items an SM holds at
+  once), the shared-memory hit budget of a seeding CTA and the candidate
+  capacity of a work item.  None of these changes what is computed, so every
+  point must reproduce the outputs of the starting point byte for byte; a
+  point that does not is rejected and reported as a defect (an overflowing
+  candidate capacity shows up this way too).  Search: coordinate descent over
+  the knobs, a few passes.
+
+* Window widths -- the two-hit window scale (Eq. tolHp), the third-hit
+  curvature band (m_lo, m_hi) and the x-layer extension tolerance.  These do
+  change the result.  Each point is scored by its time and by the track
+  finding efficiency and ghost rate measured against the calibration batch's
+  truth labels; the fastest point whose efficiency is within `eff_drop` of the
+  paper setting and whose ghost rate is within `ghost_rise` of it is picked.
+  Agreement of every grid point with the FP64 reference implementation at the
+  same configuration values is checked by the test suite, not here.
+
+The result is a dict of st_config overrides; `st.st_config_default(**tuned)`
+applies it.  `python -m paper_2606_14480_gb300.autotune --help` runs it on a
+synthetic workload and writes the overrides to a JSON file.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import st
+
+# launch-shape knobs and the values tried for each (first value of each list
+# that equals the starting configuration is where the search begins)
+LAUNCH_SPACE: Dict[str, Sequence[int]] = {
+    "threads_seed": (128, 256, 512),
+    "threads_build": (256, 512),
+    "threads_match": (128, 256, 512),
+    "ctas_per_sm": (0, 1, 2, 3),
+    "smem_hits": (1536, 2048, 3072),
+    "cand_cap": (2048, 4096),
+}
+
+# window grid: (dx3_scale, m_lo, m_hi, ext_tol); the first point is the
+# paper setting every other point is compared with
+WINDOW_GRID: List[Dict[str, float]] = [
+    {"dx3_scale": s, "m_lo": lo, "m_hi": hi, "ext_tol": 1.0}
+    for s in (1.0, 0.9, 0.8)
+    for lo, hi in ((0.5, 1.5), (0.6, 1.4), (0.7, 1.3))
+]
+
+
+@dataclass
+class Calibration:
+    """A batch in the library's CSR layout plus optional truth labels.
+
+    hit_track: global truth-track id of each hit (-1 for noise).
+    reconstructible: the truth-track ids an efficient seeding must find.
+    """
+
+    ev_off: np.ndarray
+    x: np.ndarray
+    zone: np.ndarray
+    velo_off: np.ndarray
+    velo: np.ndarray
+    hit_track: Optional[np.ndarray] = None
+    reconstructible: Optional[np.ndarray] = None
+
+    @property
+    def n_events(self) -> int:
+        return len(self.ev_off) - 1
+
+    @property
+    def n_hits(self) -> int:
+        return int(self.ev_off[-1])
+
+
+@dataclass
+class Point:
+    overrides: Dict[str, float]
+    ms: float
+    ok: bool
+    eff: Optional[float] = None
+    ghost: Optional[float] = None
+    note: str = ""
+
+
+@dataclass
+class TuneResult:
+    best: Dict[str, float]
+    best_ms: float
+    start_ms: float
+    points: List[Point] = field(default_factory=list)
+    seconds: float = 0.0
+
+    def report(self) -> dict:
+        return {"best": self.best, "best_ms": self.best_ms, "start_ms": self.start_ms,
+                "points": len(self.points), "rejected": sum(not p.ok for p in self.points),
+                "seconds": self.seconds}
+
+
+class _Bench:
+    """The calibration batch on the device and a timer for one configuration."""
+
+    def __init__(self, calib: Calibration, device: int, reps: int, flush_mb: int):
+        import torch
+        self.torch = torch
+        self.calib = calib
+        self.device = device
+        self.dev = torch.device("cuda", device)
+        self.db = st.DeviceBatch(calib.ev_off, calib.x, calib.zone, calib.velo_off, calib.velo, device=self.dev)
+        self.cap = max(1024, calib.n_hits // 4)
+        self.reps = reps
+        self.flush = torch.empty(flush_mb << 20, dtype=torch.uint8, device=self.dev)
+
+    def run(self, cfg: st.StConfig, keep_outputs: bool):
+        """Median time (ms) of a graph replay and, if asked, the outputs."""
+        torch = self.torch
+        ctx = st.Context(cfg, device=self.device)
+        try:
+            out = st.DeviceOutputs(self.db.n_events, self.cap, device=self.dev)
+            ctx.st_reserve(self.db.n_events, self.db.n_events * self.db.max_hits, self.db.max_hits, self.cap)
+            g = ctx.st_graph_create(self.db.hits, self.db.velo_s, out.seeds, out.long)
+            try:
+                stream = torch.cuda.current_stream(self.dev)
+                for _ in range(2):
+                    g.st_graph_launch(stream)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                ts = []
+                for _ in range(self.reps):
+                    self.flush.fill_(1)
+                    e0.record(stream)
+                    g.st_graph_launch(stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+            finally:
+                g.close()
+            res = out.to_numpy() if keep_outputs else None
+            return float(np.median(ts)), res
+        finally:
+            ctx.close()
+
+
+def _same(a: dict, b: dict) -> bool:
+    return all(np.array_equal(a[k], b[k]) for k in a)
+
+
+def quality(calib: Calibration, out: dict, purity: float = 0.7):
+    """(efficiency, ghost rate) of the seeds in `out` against the truth labels.
+
+    A seed belongs to the truth track that owns most of its hits if that
+    share is at least `purity`, else it is a ghost.  Efficiency is the share
+    of reconstructible tracks that own at least one seed."""
+    if calib.hit_track is None or calib.reconstructible is None:
+        return None, None
+    ev = out["ev_off"].astype(np.int64)
+    ns = int(ev[-1])
+    if ns == 0:
+        return 0.0, 0.0
+    hits = out["hits"][:ns].astype(np.int64)
+    seed_ev = np.repeat(np.arange(len(ev) - 1), np.diff(ev))
+    valid = hits >= 0
+    gidx = np.where(valid, hits + calib.ev_off[seed_ev][:, None], 0)
+    ids = np.where(valid, calib.hit_track[gidx], -2)
+    same = (ids[:, :, None] == ids[:, None, :]) & valid[:, :, None] & valid[:, None, :]
+    cnt = same.sum(2)
+    j = cnt.argmax(1)
+    top = ids[np.arange(ns), j]
+    share = cnt[np.arange(ns), j] / np.maximum(valid.sum(1), 1)
+    good = (top >= 0) & (share >= purity)
+    found = np.intersect1d(np.unique(top[good]), calib.reconstructible)
+    eff = len(found) / max(1, len(calib.reconstructible))
+    return float(eff), float(1.0 - good.mean())
+
+
+def tune_launch(base: Optional[dict] = None, calib: Optional[Calibration] = None, *, device: int = 0,
+                space: Dict[str, Sequence[int]] = LAUNCH_SPACE, passes: int = 2, reps: int = 5,
+                flush_mb: int = 256, bench: Optional[_Bench] = None) -> TuneResult:
+    """Coordinate descent over the launch-shape knobs.  `base` holds st_config
+    overrides that stay fixed (e.g. calibrated constants or window widths)."""
+    t0 = time.perf_counter()
+    base = dict(base or {})
+    b = bench or _Bench(calib, device, reps, flush_mb)
+    cur = {k: getattr(st.st_config_default(**base), k) for k in space}
+    ms0, ref = b.run(st.st_config_default(**base, **cur), keep_outputs=True)
+    res = TuneResult(best=dict(cur), best_ms=ms0, start_ms=ms0)
+    res.points.append(Point(dict(cur), ms0, True, note="start"))
+    tried = {tuple(sorted(cur.items())): ms0}
+    for _ in range(passes):
+        improved = False
+        for k, values in space.items():
+            for v in values:
+                cand = dict(res.best, **{k: v})
+                key = tuple(sorted(cand.items()))
+                if key in tried:
+                    continue
+                try:
+                    ms, out = b.run(st.st_config_default(**base, **cand), keep_outputs=True)
+                except st.StError as exc:
+                    res.points.append(Point(cand, float("nan"), False, note=f"rejected by the library: {exc}"))
+                    tried[key] = float("inf")
+                    continue
+                ok = _same(out, ref)
+                res.points.append(Point(cand, ms, ok, note="" if ok else "outputs differ from the start point"))
+                tried[key] = ms if ok else float("inf")
+                if ok and ms < res.best_ms * 0.99:
+                    res.best, res.best_ms, improved = cand, ms, True
+        if not improved:
+            break
+    res.seconds = time.perf_counter() - t0
+    return res
+
+
+def tune_windows(base: Optional[dict] = None, calib: Optional[Calibration] = None, *, device: int = 0,
+                 grid: Sequence[Dict[str, float]] = WINDOW_GRID, eff_drop: float = 0.002,
+                 ghost_rise: float = 0.002, reps: int = 5, flush_mb: int = 256,
+                 bench: Optional[_Bench] = None) -> TuneResult:
+    """Timed and truth-scored sweep of the window grid; the first grid point
+    is the reference setting."""
+    t0 = time.perf_counter()
+    base = dict(base or {})
+    b = bench or _Bench(calib, device, reps, flush_mb)
+    if b.calib.hit_track is None or b.calib.reconstructible is None:
+        raise ValueError("window tuning needs truth labels (hit_track, reconstructible)")
+    pts = []
+    for w in grid:
+        ms, out = b.run(st.st_config_default(**base, **w), keep_outputs=True)
+        eff, gh = quality(b.calib, out)
+        pts.append(Point(dict(w), ms, True, eff, gh))
+    ref = pts[0]
+    best = ref
+    for p in pts[1:]:
+        p.ok = p.eff >= ref.eff - eff_drop and p.ghost <= ref.ghost + ghost_rise
+        if not p.ok:
+            p.note = "outside the efficiency / ghost budget"
+        elif p.ms < best.ms:
+            best = p
+    res = TuneResult(best=dict(best.overrides), best_ms=best.ms, start_ms=ref.ms, points=pts)
+    res.seconds = time.perf_counter() - t0
+    return res
+
+
+def autotune(base: Optional[dict], calib: Calibration, *, device: int = 0, windows: bool = True,
+             reps: int = 5, flush_mb: int = 256, **kw):
+    """Window widths first (at the starting launch shapes), then the launch
+    shapes at the picked widths.  Returns (overrides, report)."""
+    b = _Bench(calib, device, reps, flush_mb)
+    base = dict(base or {})
+    report = {}
+    if windows:
+        wr = tune_windows(base, bench=b, **{k: v for k, v in kw.items() if k in ("grid", "eff_drop", "ghost_rise")})
+        base.update(wr.best)
+        report["windows"] = wr.report()
+        report["windows"]["grid"] = [{"overrides": p.overrides, "ms": p.ms, "eff": p.eff, "ghost": p.ghost,
+                                      "ok": p.ok} for p in wr.points]
+    lr = tune_launch(base, bench=b, **{k: v for k, v in kw.items() if k in ("space", "passes")})
+    base.update(lr.best)
+    report["launch"] = lr.report()
+    report["launch"]["defects"] = [p.overrides for p in lr.points if not p.ok]
+    return base, report
+
+
+def calibration_from_synth(batch, p_min_gev: float = 3.0, min_layers: int = 10) -> Calibration:
+    """A Calibration from a synthetic batch: reconstructible = tracks above
+    p_min_gev with hits in at least min_layers layers."""
+    lh = batch.trk["layer_hit"]
+    good = (batch.trk["p"] > p_min_gev) & ((lh >= 0).sum(1) >= min_layers)
+    return Calibration(batch.ev_off, batch.x, batch.zone, batch.velo_off, batch.velo,
+                       hit_track=batch.hit_track, reconstructible=np.nonzero(good)[0])
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--workload", default="uneven", help="synthetic workload name")
+    ap.add_argument("--events", type=int, default=2000, help="calibration events")
+    ap.add_argument("--no-windows", action="store_true", help="tune launch shapes only")
+    ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--out", default=None, help="write the overrides here (JSON)")
+    args = ap.parse_args(argv)
+    from synth import calibrate_zmatch, make_workload
+    batch = make_workload(args.workload, n_events=args.events)
+    zmx = calibrate_zmatch(7826.0)
+    tuned, report = autotune({"zmx": list(map(float, zmx))}, calibration_from_synth(batch), device=args.device,
+                             windows=not args.no_windows)
+    tuned.pop("zmx", None)
+    print(json.dumps({"overrides": tuned, "report": report}, default=float, indent=1))
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(tuned, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -903,24 +903,55 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ GatherArg
     if (threadIdx.x == 0) A.ev_off[A.n_events] = static_cast<int32_t>(carry);
 }
 
+// One block per event: the event's records come from the pool ranges of its
+// two (event, half) items and go to one contiguous range of each output
+// array, so every array is copied as a flat run (16-byte words when all
+// output arrays allow it).
+template <bool kVec>
 __global__ void __launch_bounds__(256) k_gather(const __grid_constant__ GatherArgs A) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
-    for (int64_t e = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); e < A.n_events; e += nw) {
+    for (int64_t e = blockIdx.x; e < A.n_events; e += gridDim.x) {
         const int c0 = A.item_count[2 * e], c1 = A.item_count[2 * e + 1];
-        const int s0 = A.item_start[2 * e], s1 = A.item_start[2 * e + 1];
+        const int n = c0 + c1;
+        if (n == 0) continue;
+        const int64_t s0 = A.item_start[2 * e], s1 = A.item_start[2 * e + 1];
         const int64_t d0 = A.ev_off[e];
-        for (int k = lane; k < c0 + c1; k += 32) {
-            const int64_t src = k < c0 ? s0 + k : s1 + (k - c0);
-            const int64_t dst = d0 + k;
-#pragma unroll
-            for (int q = 0; q < 12; ++q) A.hits[dst * 12 + q] = A.pool_hits[src * 12 + q];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) A.params[dst * 8 + q] = A.pool_params[src * 8 + q];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) A.state[dst * 4 + q] = A.pool_state[src * 4 + q];
-            A.n_hits[dst * 2] = A.pool_n[src * 2];
-            A.n_hits[dst * 2 + 1] = A.pool_n[src * 2 + 1];
+        auto src = [&](int k) { return k < c0 ? s0 + k : s1 + (k - c0); };
+        if (kVec) {
+            const uint4* ph = reinterpret_cast<const uint4*>(A.pool_hits);
+            const uint4* pp = reinterpret_cast<const uint4*>(A.pool_params);
+            const uint4* ps = reinterpret_cast<const uint4*>(A.pool_state);
+            uint4* oh = reinterpret_cast<uint4*>(A.hits);
+            uint4* op = reinterpret_cast<uint4*>(A.params);
+            uint4* os = reinterpret_cast<uint4*>(A.state);
+            for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
+                const int k = i / 3, q = i - 3 * k;
+                oh[(d0 + k) * 3 + q] = ph[src(k) * 3 + q];
+            }
+            for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+                const int k = i >> 1, q = i & 1;
+                op[(d0 + k) * 2 + q] = pp[src(k) * 2 + q];
+            }
+            for (int k = threadIdx.x; k < n; k += blockDim.x) os[d0 + k] = ps[src(k)];
+            const uint16_t* pn = reinterpret_cast<const uint16_t*>(A.pool_n);
+            uint16_t* on = reinterpret_cast<uint16_t*>(A.n_hits);
+            for (int k = threadIdx.x; k < n; k += blockDim.x) on[d0 + k] = pn[src(k)];
+        } else {
+            for (int i = threadIdx.x; i < 12 * n; i += blockDim.x) {
+                const int k = i / 12, q = i - 12 * k;
+                A.hits[(d0 + k) * 12 + q] = A.pool_hits[src(k) * 12 + q];
+            }
+            for (int i = threadIdx.x; i < 8 * n; i += blockDim.x) {
+                const int k = i >> 3, q = i & 7;
+                A.params[(d0 + k) * 8 + q] = A.pool_params[src(k) * 8 + q];
+            }
+            for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) {
+                const int k = i >> 2, q = i & 3;
+                A.state[(d0 + k) * 4 + q] = A.pool_state[src(k) * 4 + q];
+            }
+            for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
+                const int k = i >> 1, q = i & 1;
+                A.n_hits[(d0 + k) * 2 + q] = A.pool_n[src(k) * 2 + q];
+            }
         }
     }
 }
@@ -1185,9 +1216,15 @@ cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
     k_scan<<<1, 1024, 0, s>>>(a);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    const int64_t warps = a.n_events;
-    const int grid = static_cast<int>(std::min<int64_t>((warps + 7) / 8, 4096));
-    if (grid > 0) k_gather<<<grid, 256, 0, s>>>(a);
+    const int grid = static_cast<int>(std::min<int64_t>(a.n_events, 8192));
+    if (grid <= 0) return cudaSuccess;
+    // pool arrays are 256-byte aligned; the caller's output arrays may not be
+    const uintptr_t mis = (reinterpret_cast<uintptr_t>(a.hits) | reinterpret_cast<uintptr_t>(a.params) |
+                           reinterpret_cast<uintptr_t>(a.state)) & 15u;
+    if (mis == 0 && (reinterpret_cast<uintptr_t>(a.n_hits) & 1u) == 0)
+        k_gather<true><<<grid, 256, 0, s>>>(a);
+    else
+        k_gather<false><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
