@@ -370,21 +370,29 @@ def main():
         rc, _ = ctx2.pipeline_poll(t, hb.seeds, hb.long, 60_000_000)
         assert rc == st.ST_OK, rc
     h2d = 8 * (n_ev + 1) * 2 + 8 * batch.n_hits + 16 * batch.velo.shape[0]
-    e2e_t = []
+    # two batches in flight: the next batch's inputs are copied in while the
+    # current one runs; every step's results are read back to the host
+    depth = 2
+    pending = []
+    if ws > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        t = ctx2.pipeline_submit(hh, hv)
-        rc, info = ctx2.pipeline_poll(t, hb.seeds, hb.long, 60_000_000)
+        pending.append(ctx2.pipeline_submit(hh, hv))
+        if len(pending) >= depth:
+            rc, info = ctx2.pipeline_poll(pending.pop(0), hb.seeds, hb.long, 60_000_000)
+            assert rc == st.ST_OK, rc
+    while pending:
+        rc, info = ctx2.pipeline_poll(pending.pop(0), hb.seeds, hb.long, 60_000_000)
         assert rc == st.ST_OK, rc
-        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = time.perf_counter() - t0
     ns = int(hb.ev_off[-1])
     d2h = 4 * (n_ev + 1) + 8 * n_ev + ns * (48 + 32 + 16 + 2 + 8)
-    e2e_total = float(np.sum(e2e_t))
     e2e_total = max_over_ranks(e2e_total, device=dev)
     log(f"e2e: {1000 * e2e_total / args.steps:.3f} ms/step")
     result["e2e"] = {"value": job_rate(n_ev * args.steps, ws, e2e_total), "unit": "events/s",
                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                     "api": "pipeline_submit + pipeline_poll, host buffers, one batch in flight"}
+                     "api": "pipeline_submit + pipeline_poll, pageable host buffers, two batches in flight"}
 
     if rank == 0 and ws == 1:
         # ---------------- plain per-event launch

@@ -463,7 +463,7 @@ size_t seed_smem_bytes(int threads, int smem_hits, int tbl_smem, int key_smem) {
 size_t seed_slot_bytes(int cand_cap, int max_xhits) {
     return align16(sizeof(int) * 16 * size_t(cand_cap)) +
            sizeof(ull) * (size_t(max_xhits) + cand_cap + size_t(kTripPerCand) * cand_cap) +
-           16 + sizeof(uint4) * kUvStore + sizeof(float) * 6 * size_t(cand_cap) + 8 +
+           16 + (sizeof(uint4) + sizeof(uint2)) * kUvStore + sizeof(float) * 6 * size_t(cand_cap) + 8 +
            sizeof(ull) * kTripLocal * kMaxThreads;
 }
 
@@ -510,7 +510,8 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     // hits + ty of stored UV chains (16-byte aligned: the clone table before it
     // has max_xhits 8-byte entries, which may be odd)
     uint4* vstore = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(trip + TC) + 15) & ~uintptr_t(15));
-    float* g_xs = reinterpret_cast<float*>(vstore + kUvStore);
+    uint2* vmeta = reinterpret_cast<uint2*>(vstore + kUvStore);  // (seed, pass | initial hit << 1)
+    float* g_xs = reinterpret_cast<float*>(vmeta + kUvStore);
     ull* tloc = reinterpret_cast<ull*>(g_xs + 6 * CC) + tid * kTripLocal;  // this thread's triplet buffer
     __shared__ int s_nvalid;
 
@@ -739,12 +740,14 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
         }
         if (tid == 0) s_nvalid = 0;
         __syncthreads();
+        // chains are numbered pass-major (all pass A chains, then pass B) so
+        // that a warp's chains mostly share their initial layer
         const int nuv = 2 * nk;
         for (int b = 0; b < nuv; b += T) {
             const int i = b + tid;
             int cntc = 0, lo = 0;
             if (i < nuv) {
-                const int j = i >> 1, pass = i & 1;
+                const int pass = i >= nk, j = i - (pass ? nk : 0);
                 const int ui = P.uv_init[pass];
                 const float Xi = Xs[6 * j + ui];
                 const float t = P.ut[ui];
@@ -773,17 +776,13 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                         nxt = o + 1 < T ? sPS[o + 1] : tot;
                         kinit = sA[o];
                     }
-                    const int it2 = sB[o];
-                    const int j = it2 >> 1, pass = it2 & 1;
+                    const int i2 = sB[o];
+                    const int pass = i2 >= nk, j = i2 - (pass ? nk : 0);
                     UV u;
                     uv_chain(P, X, szl, lut, Xs + 6 * j, pass, kinit, u);
                     if (u.n >= P.n_uv_min) {
                         ++ctr[6];
-                        const int k = kept[j];
-                        const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
-                        const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
-                        uv_fit(P, X, th, dth, u);
-                        int sidx = atomicAdd(&s_nvalid, 1);
+                        const int sidx = atomicAdd(&s_nvalid, 1);
                         if (sidx < kUvStore) {
                             uint4 r;
                             r.x = (unsigned(u.pos[0] + 1) & 0xFFFFu) | (unsigned(u.pos[1] + 1) << 16);
@@ -791,16 +790,43 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                             r.z = (unsigned(u.pos[4] + 1) & 0xFFFFu) | (unsigned(u.pos[5] + 1) << 16);
                             r.w = __float_as_uint(u.tyr);
                             vstore[sidx] = r;
+                            vmeta[sidx] = make_uint2(unsigned(j), unsigned(pass) | (unsigned(kinit) << 1));
                         } else {
-                            sidx = kUvNotStored;
+                            // store full: fit here; the winner is searched again at output
+                            const int k = kept[j];
+                            const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
+                            const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
+                            uv_fit(P, X, th, dth, u);
+                            atomicMin(&ukey[j], uv_key(u.n, u.chi2, pass, kinit, kUvNotStored));
                         }
-                        atomicMin(&ukey[j], uv_key(u.n, u.chi2, pass, kinit, sidx));
                     }
                     ++kinit;
                 }
             }
             __syncthreads();
         }
+        // the stored chains' fits, one per thread
+        const int nvs = min(s_nvalid, kUvStore);
+        for (int q = tid; q < nvs; q += T) {
+            const uint4 v = vstore[q];
+            const uint2 mt = vmeta[q];
+            const unsigned w[3] = {v.x, v.y, v.z};
+            UV u;
+            u.n = 0;
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                u.pos[r] = static_cast<int>((w[r >> 1] >> (16 * (r & 1))) & 0xFFFFu) - 1;
+                u.n += u.pos[r] >= 0;
+            }
+            u.tyr = __uint_as_float(v.w);
+            const int j = static_cast<int>(mt.x);
+            const int k = kept[j];
+            const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
+            const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
+            uv_fit(P, X, th, dth, u);
+            atomicMin(&ukey[j], uv_key(u.n, u.chi2, static_cast<int>(mt.y & 1u), static_cast<int>(mt.y >> 1), q));
+        }
+        __syncthreads();
 
         // ------------------------------------------------------------ seeds
         int nseed = 0;
