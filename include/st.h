@@ -258,7 +258,7 @@ int st_read_counters(st_ctx* ctx, st_counters* out, int reset);
  * current for the calling thread.  The results equal seeding_run's.
  * Limits: max_hits_per_event <= 6144, and the batch must fit the array:
  * about 8*n_events*max_hits_per_event + 98*seeds->cap bytes plus one
- * candidate store of 64*cand_cap + 8*(max_hits_per_event + cand_cap) bytes
+ * candidate store of about 112*cand_cap + 8*max_hits_per_event + 360 KB
  * (e.g. 128 events of up to 4096 hits with 40 000 seeds fit); otherwise it
  * returns ST_OVERFLOW and writes nothing.  A NUL-terminated message goes to
  * err (may be NULL) on every failure.

@@ -46,7 +46,7 @@ LAUNCH_SPACE: Dict[str, Sequence[int]] = {
     "threads_build": (256, 512),
     "threads_match": (128, 256, 512),
     "ctas_per_sm": (0, 1, 2, 3),
-    "smem_hits": (1536, 2048, 3072),
+    "smem_hits": (1024, 1536, 2048, 3072),
     "cand_cap": (2048, 4096),
 }
 

@@ -172,6 +172,35 @@ __device__ __forceinline__ int block_exscan(int v, int* tmp, int& total) {
     return res;
 }
 
+// The same scan with one barrier: every warp adds up the partial sums of the
+// warps before it itself.  Consecutive calls alternate between the two halves
+// of `buf` (>= 34 ints) under the block-uniform toggle `par`, so a call never
+// overwrites partial sums that a slower thread may still read from the
+// previous call (the barrier of the call in between orders them).
+__device__ __forceinline__ int block_exscan1(int v, int* buf, int& par, int& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    int* t = buf + (par ? 17 : 0);
+    par ^= 1;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) t[wid] = x;
+    __syncthreads();
+    int w = lane < nw ? t[lane] : 0;
+    int before = lane < wid ? w : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+    }
+    total = w;
+    return x - v + before;
+}
+
 __device__ __forceinline__ int warp_sum(int v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

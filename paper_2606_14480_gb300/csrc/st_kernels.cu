@@ -463,12 +463,18 @@ size_t seed_smem_bytes(int threads, int smem_hits, int tbl_smem, int key_smem) {
 size_t seed_slot_bytes(int cand_cap, int max_xhits) {
     return align16(sizeof(int) * 16 * size_t(cand_cap)) +
            sizeof(ull) * (size_t(max_xhits) + cand_cap + size_t(kTripPerCand) * cand_cap) +
-           16 + (sizeof(uint4) + sizeof(uint2)) * kUvStore + sizeof(float) * 6 * size_t(cand_cap) + 8 +
+           16 + (2 * sizeof(uint4) + sizeof(uint2)) * kUvStore + sizeof(float) * 6 * size_t(cand_cap) + 8 +
            sizeof(ull) * kTripLocal * kMaxThreads;
 }
 
-// two CTAs of 512 threads (four of 256) per SM: 64 registers per thread
-__global__ void __launch_bounds__(kMaxThreads, 2)
+// Two instantiations: CTAs of up to 256 threads with five per SM (48
+// registers per thread: more resident warps hide the shared-memory and
+// barrier latency better than fewer spills would), and up to 512 threads with
+// two per SM (64 registers).
+constexpr int kSeedBlocks256 = 5;
+
+template <int kT, int kB>
+__global__ void __launch_bounds__(kT, kB)
 k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = blockDim.x, tid = threadIdx.x;
@@ -510,10 +516,12 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     // hits + ty of stored UV chains (16-byte aligned: the clone table before it
     // has max_xhits 8-byte entries, which may be odd)
     uint4* vstore = reinterpret_cast<uint4*>((reinterpret_cast<uintptr_t>(trip + TC) + 15) & ~uintptr_t(15));
-    uint2* vmeta = reinterpret_cast<uint2*>(vstore + kUvStore);  // (seed, pass | initial hit << 1)
+    float4* vfit = reinterpret_cast<float4*>(vstore + kUvStore);   // (chi2_y, beta, wm, zm) of the fit
+    uint2* vmeta = reinterpret_cast<uint2*>(vfit + kUvStore);      // (seed, pass | initial hit << 1)
     float* g_xs = reinterpret_cast<float*>(vmeta + kUvStore);
     ull* tloc = reinterpret_cast<ull*>(g_xs + 6 * CC) + tid * kTripLocal;  // this thread's triplet buffer
     __shared__ int s_nvalid;
+    int spar = 0;  // which half of tmp the next block scan uses
 
     ull ctr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
@@ -587,7 +595,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             }
             ctr[0] += np;
             int tot_p;
-            const int ps = block_exscan(np, tmp, tot_p);
+            const int ps = block_exscan1(np, tmp, spar, tot_p);
             sPS[tid] = ps;
             sA[tid] = lo3;
             sB[tid] = tag;
@@ -633,7 +641,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             const int nt = walk(false, 0);
             const int again = __syncthreads_or(nt > kTripLocal);
             int tot_t;
-            int wofs = block_exscan(nt, tmp, tot_t);
+            int wofs = block_exscan1(nt, tmp, spar, tot_t);
             ctr[1] += nt;
             if (ntrip + tot_t > TC) overflow = true;
             if (!overflow) {
@@ -661,7 +669,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     ctr[2] += code >= 1;
                 }
                 int tot;
-                const int co = block_exscan(code == 2 ? 1 : 0, tmp, tot);
+                const int co = block_exscan1(code == 2 ? 1 : 0, tmp, spar, tot);
                 if (code == 2) {
                     const int ci = ncand + co;
                     if (ci < CC) {
@@ -720,7 +728,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 keep = owned >= 3 || (owned >= 2 && c_nx[k] == 6);
             }
             int tot;
-            const int o = block_exscan(keep, tmp, tot);
+            const int o = block_exscan1(keep, tmp, spar, tot);
             if (keep) kept[nk + o] = k;
             nk += tot;
         }
@@ -759,7 +767,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             }
             ctr[5] += cntc;
             int tot;
-            const int ps = block_exscan(cntc, tmp, tot);
+            const int ps = block_exscan1(cntc, tmp, spar, tot);
             sPS[tid] = ps;
             sA[tid] = lo;
             sB[tid] = i;
@@ -824,6 +832,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
             const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
             uv_fit(P, X, th, dth, u);
+            vfit[q] = make_float4(u.chi2, u.beta, u.wm, u.zm);
             atomicMin(&ukey[j], uv_key(u.n, u.chi2, static_cast<int>(mt.y & 1u), static_cast<int>(mt.y >> 1), q));
         }
         __syncthreads();
@@ -856,7 +865,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             const int j = b + tid;
             const int has = j < nk && ukey[j] != ~0ull;
             int tot;
-            const int o = block_exscan(has, tmp, tot);
+            const int o = block_exscan1(has, tmp, spar, tot);
             if (has) {
                 const int64_t r = int64_t(s_start) + wbase + o;
                 const ull key = ukey[j];
@@ -875,11 +884,16 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                         u.n += u.pos[q] >= 0;
                     }
                     u.tyr = __uint_as_float(v.w);
+                    const float4 f = vfit[sidx];
+                    u.chi2 = f.x;
+                    u.beta = f.y;
+                    u.wm = f.z;
+                    u.zm = f.w;
                 } else {
                     uv_chain(P, X, szl, lut, Xs + 6 * j, static_cast<int>((key >> 29) & 1),
                              static_cast<int>((key >> 13) & 0xFFFFu), u);
+                    uv_fit(P, X, th, dth, u);
                 }
-                uv_fit(P, X, th, dth, u);
                 int32_t* ho = A.pool_hits + r * 12;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
@@ -1199,8 +1213,8 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
 // Raise each kernel's dynamic shared-memory ceiling to what the device allows
 // next to the kernel's own static shared memory (opt-in maximum - static).
 cudaError_t set_smem_limits(size_t optin) {
-    const void* fns[] = {reinterpret_cast<const void*>(k_build), reinterpret_cast<const void*>(k_seed),
-                         reinterpret_cast<const void*>(k_match)};
+    const void* fns[] = {reinterpret_cast<const void*>(k_build), reinterpret_cast<const void*>(k_seed<256, kSeedBlocks256>),
+                         reinterpret_cast<const void*>(k_seed<kMaxThreads, 2>), reinterpret_cast<const void*>(k_match)};
     for (const void* f : fns) {
         cudaFuncAttributes fa;
         cudaError_t err = cudaFuncGetAttributes(&fa, f);
@@ -1219,7 +1233,10 @@ int build_blocks_per_sm(int threads, size_t smem) {
 }
 int seed_blocks_per_sm(int threads, size_t smem) {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed, threads, smem);
+    if (threads <= 256)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed<256, kSeedBlocks256>, threads, smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed<kMaxThreads, 2>, threads, smem);
     return n;
 }
 int match_blocks_per_sm(int threads, size_t smem) {
@@ -1234,7 +1251,11 @@ cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int t
 }
 
 cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s) {
-    k_seed<<<grid, threads, seed_smem_bytes(threads, a.smem_hits, a.tbl_smem, a.key_smem), s>>>(P, a);
+    const size_t smem = seed_smem_bytes(threads, a.smem_hits, a.tbl_smem, a.key_smem);
+    if (threads <= 256)
+        k_seed<256, kSeedBlocks256><<<grid, threads, smem, s>>>(P, a);
+    else
+        k_seed<kMaxThreads, 2><<<grid, threads, smem, s>>>(P, a);
     return cudaGetLastError();
 }
 

@@ -142,7 +142,7 @@ extern "C" void st_config_default(st_config* c) {
     c->threads_build = 512;
     c->threads_match = 256;
     c->ctas_per_sm = 0;
-    c->smem_hits = 2048;
+    c->smem_hits = 1536;
     c->cand_cap = 4096;
 }
 
@@ -519,12 +519,13 @@ extern "C" int st_create(const st_config* cfg, int device, st_ctx** out) {
     ctx->smem_optin = optin;
     const st_config& c = *cfg;
     ctx->tbl_smem = c.smem_hits / 2;
-    ctx->key_smem = 512;
+    ctx->key_smem = std::max(64, c.smem_hits / 4);  // kept seeds whose UV keys and stereo x stay in shared memory
     ctx->velo_smem = 512;
     ctx->seed_smem = seed_smem_bytes(c.threads_seed, c.smem_hits, ctx->tbl_smem, ctx->key_smem);
     ctx->match_smem = match_smem_bytes(ctx->velo_smem);
     ctx->build_smem_max = build_smem_bytes(512, kBuildSmemHits);
-    if (ctx->seed_smem + 64 > ctx->smem_optin || ctx->build_smem_max + 64 > ctx->smem_optin) {
+    // 2 KB of margin for the kernels' static shared memory
+    if (ctx->seed_smem + 2048 > ctx->smem_optin || ctx->build_smem_max + 2048 > ctx->smem_optin) {
         delete ctx;
         return ST_EINVAL;
     }
