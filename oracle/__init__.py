@@ -57,6 +57,8 @@ class OrConfig(C.Structure):
         ("presel_scale", C.c_double), ("tol_scale", C.c_double), ("tolx", C.c_double * 3),
         ("toly", C.c_double * 3), ("tol_tx", C.c_double), ("tol_ty", C.c_double),
         ("chi2_match_max", C.c_double), ("velo_unique", C.c_int32), ("pad2", C.c_int32),
+        ("uv_mode", C.c_int32), ("hough_bins", C.c_int32), ("hough_fine", C.c_int32),
+        ("hough_clusters", C.c_int32), ("hough_ty_max", C.c_double), ("hough_ty_in", C.c_double),
     ]
 
 
@@ -82,7 +84,7 @@ class OrCounters(C.Structure):
 
 LEDGER_KINDS = {1: "pair_win", 2: "trip_win", 3: "ext_tol", 4: "ext_tie", 5: "chi2x", 6: "clone",
                 7: "uv_win", 8: "uv_tol", 9: "uv_tie", 10: "uv_sel", 11: "m_presel", 12: "m_chi2",
-                13: "m_tie"}
+                13: "m_tie", 14: "hough_bin"}
 
 _P = C.c_void_p
 

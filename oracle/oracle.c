@@ -93,6 +93,12 @@ void or_config_default(or_config* c) {
     c->tol_ty = 1.0 / 937.5;
     c->chi2_match_max = 2.0;
     c->velo_unique = 0;
+    c->uv_mode = 0;          /* the paper's default UV approach */
+    c->hough_bins = 64;      /* Hough variant: not given in the paper (readings) */
+    c->hough_fine = 4;
+    c->hough_clusters = 8;   /* "up to eight of the best bins" */
+    c->hough_ty_max = 0.33;
+    c->hough_ty_in = 0.01;
 }
 
 static int config_ok(const or_config* c) {
@@ -107,6 +113,10 @@ static int config_ok(const or_config* c) {
     }
     if (c->n_uv_min < 2 || c->n_uv_min > 6) return 0;
     if (!(c->p_min > 0) || !(c->sigma_x > 0) || !(c->sigma_y > 0)) return 0;
+    if (c->uv_mode < 0 || c->uv_mode > 1) return 0;
+    if (c->hough_bins < 2 || c->hough_bins > 64 || c->hough_fine < 1 || c->hough_fine > 8 ||
+        c->hough_clusters < 1 || c->hough_clusters > 8 || !(c->hough_ty_max + c->hough_ty_in > 0))
+        return 0;
     return 1;
 }
 
@@ -666,6 +676,131 @@ static int uv_seed(ev_t* E, int half, const cand_t* cd, uvc_t* best_out) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* UV seeding, Hough-cluster variant, Section 3.4                           */
+/* ------------------------------------------------------------------------ */
+/* Every stereo hit of the seed's half whose y lies in the same window as the
+ * iterative variant's first layer is mapped to t_y = y / z (a straight line
+ * from the origin) and to a coarse bin of [ty_lo, ty_hi) (hough_bins bins;
+ * half 1: [-ty_in, ty_max], half 0 mirrored).  A cluster b is the pair of
+ * bins (b, b+1); its population is the number of stereo LAYERS with a hit in
+ * either bin.  The clusters with the largest populations (at least n_uv_min;
+ * ties to the smaller b) are kept, up to hough_clusters of them, and each is
+ * divided into hough_fine t_y hypotheses at the centres of equal sub-bins.
+ * For each hypothesis the closest hit within uv_tol is attached in every
+ * stereo layer; combinations with at least n_uv_min hits are fitted as in the
+ * iterative variant and the best is chosen by the same rule (most hits, then
+ * smallest chi2_y), ties to the earlier hypothesis (cluster rank, then
+ * sub-bin). */
+static int uv_seed_hough(ev_t* E, int half, const cand_t* cd, uvc_t* best_out) {
+    const or_config* c = E->c;
+    const double ylo = half ? -c->uv_y_overlap : -c->uv_y_max;
+    const double yhi = half ? c->uv_y_max : c->uv_y_overlap;
+    const double ty_lo = half ? -c->hough_ty_in : -c->hough_ty_max;
+    const double ty_hi = half ? c->hough_ty_max : c->hough_ty_in;
+    const int NB = c->hough_bins, F = c->hough_fine;
+    const double w = (ty_hi - ty_lo) / NB;
+    int32_t ctx[7];
+    int nctx = 0;
+    for (int s = 0; s < 6; ++s)
+        if (cd->hits[s] >= 0) ctx[nctx++] = cd->hits[s];
+    /* hits of every stereo layer in every coarse bin */
+    int occ[6][64];
+    memset(occ, 0, sizeof(occ));
+    for (int q = 0; q < 6; ++q) {
+        const int L = UV_LAYERS[q];
+        const int zi = 2 * L + half;
+        const double zL = c->z[L], tL = c->dxdy[L];
+        const double XL = xmodel(c, cd->th, zL);
+        const double SL = xscale(c, cd->th, zL);
+        for (int k = 0; k < E->zn[zi]; ++k) {
+            const double xh = E->zl[zi][k].x;
+            ctx[nctx] = E->zl[zi][k].i;
+            const double y = (XL - xh) / tL;
+            const double S = dmax2(dmax2(SL, fabs(xh)), fabs(yhi * tL));
+            ledger_add(E, OR_L_UV_WIN, half, fmin(fabs(y - ylo), fabs(y - yhi)) * fabs(tL) / S, ctx, nctx + 1);
+            if (y < ylo || y > yhi) continue;
+            const double u = (y / zL - ty_lo) / w;
+            int b = (int)floor(u);
+            /* distance to the nearer bin edge, as an x distance in the layer */
+            const double du = fmin(u - floor(u), ceil(u) - u);
+            ledger_add(E, OR_L_HOUGH_BIN, half, du * w * zL * fabs(tL) / S, ctx, nctx + 1);
+            if (b < 0) b = 0;
+            if (b > NB - 1) b = NB - 1;
+            occ[q][b]++;
+        }
+    }
+    /* cluster populations and the kept clusters, best first */
+    int pop[64], sel[8], nsel = 0;
+    for (int b = 0; b + 1 < NB; ++b) {
+        pop[b] = 0;
+        for (int q = 0; q < 6; ++q) pop[b] += occ[q][b] + occ[q][b + 1] > 0;
+    }
+    for (int p = 6; p >= c->n_uv_min && nsel < c->hough_clusters; --p)
+        for (int b = 0; b + 1 < NB && nsel < c->hough_clusters; ++b)
+            if (pop[b] == p) sel[nsel++] = b;
+    /* hypotheses */
+    uvc_t best;
+    int have = 0;
+    nctx = 0;
+    for (int s = 0; s < 6; ++s)
+        if (cd->hits[s] >= 0) ctx[nctx++] = cd->hits[s];
+    uvc_t all[64];
+    int nall = 0;
+    for (int r = 0; r < nsel; ++r) {
+        for (int f = 0; f < F; ++f) {
+            const double ty = ty_lo + w * (sel[r] + (f + 0.5) * 2.0 / F);
+            E->cnt.uv_init++;
+            uvc_t u;
+            int n = 0;
+            for (int q = 0; q < 6; ++q) {
+                const int L = UV_LAYERS[q];
+                const double zL = c->z[L], tL = c->dxdy[L];
+                const double XL = xmodel(c, cd->th, zL);
+                const double xp = XL - tL * ty * zL;
+                const double sc = dmax2(xscale(c, cd->th, zL), fabs(tL * ty * zL));
+                u.hits[q] = closest_hit(E, 2 * L + half, xp, c->uv_tol, sc, OR_L_UV_TOL, OR_L_UV_TIE, half,
+                                        ctx, nctx);
+                n += u.hits[q] >= 0;
+            }
+            if (n < c->n_uv_min) continue;
+            E->cnt.uv_cands++;
+            double zs2[6], ys2[6], y0f, tyf;
+            int m = 0;
+            for (int q = 0; q < 6; ++q) {
+                if (u.hits[q] < 0) continue;
+                const int L = UV_LAYERS[q];
+                zs2[m] = c->z[L];
+                ys2[m] = (xmodel(c, cd->th, c->z[L]) - E->x[u.hits[q]]) / c->dxdy[L];
+                m++;
+            }
+            u.chi2 = fit_line(m, zs2, ys2, &y0f, &tyf) / (c->sigma_y * c->sigma_y);
+            u.n = m;
+            u.y0 = y0f;
+            u.ty = tyf;
+            all[nall++] = u;
+            if (!have || u.n > best.n || (u.n == best.n && u.chi2 < best.chi2)) {
+                best = u;
+                have = 1;
+            }
+        }
+    }
+    if (have && E->tau > 0) {
+        for (int k = 0; k < nall; ++k) {
+            if (all[k].n != best.n || memcmp(all[k].hits, best.hits, sizeof(best.hits)) == 0) continue;
+            double m = fabs(all[k].chi2 - best.chi2) / dmax2(dmax2(all[k].chi2, best.chi2), 1e-300);
+            int32_t hh[12];
+            for (int q = 0; q < 6; ++q) {
+                hh[q] = best.hits[q];
+                hh[6 + q] = all[k].hits[q];
+            }
+            ledger_add(E, OR_L_UV_SEL, half, m, hh, 12);
+        }
+    }
+    if (have) *best_out = best;
+    return have;
+}
+
+/* ------------------------------------------------------------------------ */
 /* event driver                                                             */
 /* ------------------------------------------------------------------------ */
 
@@ -722,7 +857,7 @@ int32_t or_seeding_event(const or_config* c, int32_t n_hits, const double* x,
             nc++;
             if (!cd->keep) continue;
             uvc_t u;
-            if (!uv_seed(&E, half, cd, &u)) continue;
+            if (!(c->uv_mode == 1 ? uv_seed_hough(&E, half, cd, &u) : uv_seed(&E, half, cd, &u))) continue;
             E.cnt.seeds++;
             if (seeds && ns < seeds_cap) {
                 or_seed* s = &seeds[ns];

@@ -68,6 +68,13 @@ typedef struct {
     double chi2_match_max;        /* 2 */
     int32_t velo_unique;          /* 1: a VELO segment serves at most one seed */
     int32_t pad2;
+    /* UV seeding, Hough-cluster variant (Section 3.4, second approach) */
+    int32_t uv_mode;              /* 0: iterative over an initial layer, 1: Hough clusters */
+    int32_t hough_bins;           /* coarse t_y bins (2..64) */
+    int32_t hough_fine;           /* t_y hypotheses per selected cluster (1..8) */
+    int32_t hough_clusters;       /* clusters kept per seed, best first (1..8) */
+    double hough_ty_max;          /* coarse range [-hough_ty_in, hough_ty_max] for half 1, */
+    double hough_ty_in;           /* mirrored for half 0 */
 } or_config;
 
 typedef struct {
@@ -90,7 +97,7 @@ enum {
     OR_L_PAIR_WIN = 1, OR_L_TRIP_WIN = 2, OR_L_EXT_TOL = 3, OR_L_EXT_TIE = 4,
     OR_L_CHI2X = 5, OR_L_CLONE = 6, OR_L_UV_WIN = 7, OR_L_UV_TOL = 8,
     OR_L_UV_TIE = 9, OR_L_UV_SEL = 10, OR_L_M_PRESEL = 11, OR_L_M_CHI2 = 12,
-    OR_L_M_TIE = 13
+    OR_L_M_TIE = 13, OR_L_HOUGH_BIN = 14
 };
 typedef struct {
     int32_t kind, half;

@@ -30,6 +30,16 @@ MUTATIONS = {
     "match_dropped_E": (" + c->zmx[4] * txV * txV;", ";"),
     "match_wrong_z": ("(xS + (zmx - c->z_state) * txS)", "(xS + (zmx - c->z_velo) * txS)"),
     "toly_no_ty": ("const double rho = txV * txV + tyV * tyV;", "const double rho = txV * txV;"),
+    "hough_single_bin": ("for (int q = 0; q < 6; ++q) pop[b] += occ[q][b] + occ[q][b + 1] > 0;",
+                         "for (int q = 0; q < 6; ++q) pop[b] += occ[q][b] > 0;"),
+    "hough_counts_hits": ("for (int q = 0; q < 6; ++q) pop[b] += occ[q][b] + occ[q][b + 1] > 0;",
+                          "for (int q = 0; q < 6; ++q) pop[b] += occ[q][b] + occ[q][b + 1];"),
+    "hough_worst_first": ("for (int p = 6; p >= c->n_uv_min && nsel < c->hough_clusters; --p)",
+                          "for (int p = c->n_uv_min; p <= 6 && nsel < c->hough_clusters; ++p)"),
+    "hough_bin_edge": ("const double ty = ty_lo + w * (sel[r] + (f + 0.5) * 2.0 / F);",
+                       "const double ty = ty_lo + w * (sel[r] + f * 2.0 / F);"),
+    "hough_y_sign": ("const double y = (XL - xh) / tL;\n            const double S = dmax2(dmax2(SL",
+                     "const double y = (xh - XL) / tL;\n            const double S = dmax2(dmax2(SL"),
     "state_slope": ("s->tx_s = cd->th[1] + cd->th[2] * (2.0 * zb + 3.0 * c->d_ratio * zb * zb);",
                     "s->tx_s = cd->th[1];"),
 }

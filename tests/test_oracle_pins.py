@@ -72,13 +72,13 @@ def check_k3_chord(L=None):
             assert dx2 == pytest.approx(oracle.k3(cfg, it, _lib=L) * c, rel=1e-7, abs=1e-9)
 
 
-def check_noise_free_recovery(L=None, zmx=None, n_events=6):
+def check_noise_free_recovery(L=None, zmx=None, n_events=6, **overrides):
     """North-star pin: noise-free, unsmeared, fully efficient tracks above
     3.5 GeV are all found, with no ghost or clone, each seed holds exactly its
     track's 12 hits, the fit returns the generating parameters to FP64
     rounding, and matching picks the track's own VELO segment."""
     b = workload("noise_free", n_events=n_events)
-    cfg = oracle.default_config(_lib=L)
+    cfg = oracle.default_config(_lib=L, **overrides)
     if zmx is not None:
         oracle.apply(cfg, {"zmx": zmx})
     for e in range(b.n_events):
@@ -315,9 +315,94 @@ def check_matching_grid(L=None, zmx=None, n_events=8):
     assert m["chi2"][0] == pytest.approx(dyo ** 2 / tol_y, rel=1e-12)
 
 
+# ---------------------------------------------------------------------------
+# Hough-cluster UV variant (Section 3.4, second approach)
+# ---------------------------------------------------------------------------
+
+def check_hough_noise_free(L=None, n_events=4):
+    """The noise-free recovery pin with the Hough-cluster UV variant: every
+    track found with its exact twelve hits and its generating t_y."""
+    check_noise_free_recovery(L, None, n_events=n_events, uv_mode=1)
+
+
+def _stereo_event(seed, ty_of_layer, extra=()):
+    """One noise-free track whose six stereo hits are placed at the given
+    t_y per stereo layer (y = t_y z), plus extra hits (layer, t_y); x-layer
+    hits are the generator's exact ones.  Returns x, zone, the track's layer
+    hits and its half."""
+    b = make_events(1, seed=seed, tracks=("fixed", 1), noise_frac=0.0, eff=1.0, sigma_x=0.0,
+                    p_range=(5.0, 50.0), velo_ghosts_per_track=0.0, velo_sigma=(0, 0))
+    x, zone = b.exact_hits_of(0)
+    x, zone = x.copy(), zone.copy()
+    tr = b.tracks_of(0)
+    lh = tr["layer_hit"][0]
+    half = int(zone[lh[0]] % 2)
+    sgn = 1.0 if half else -1.0
+    a, bb, c = tr["a"][0], tr["b"][0], tr["c"][0]
+    zl, t = DET.z_arr, DET.dxdy
+    for L, ty in ty_of_layer.items():
+        if ty is None:
+            x[lh[L]] += 500.0  # moved far from the track: acts as a noise hit
+        else:
+            x[lh[L]] = DET.x_model(a, bb, c, zl[L]) - t[L] * sgn * ty * zl[L]
+    xs, zs = [x], [zone]
+    for L, ty in extra:
+        xs.append(np.array([DET.x_model(a, bb, c, zl[L]) - t[L] * sgn * ty * zl[L]]))
+        zs.append(np.array([2 * L + half], np.int32))
+    return np.concatenate(xs), np.concatenate(zs).astype(np.int32), lh, half
+
+
+def check_hough_clusters(L=None):
+    """Constructed cases that fix each part of the Hough-cluster reading:
+    a track whose stereo hits straddle a coarse bin edge is one cluster (two
+    bins); populations count stereo LAYERS, not hits; clusters are taken best
+    first; the t_y hypotheses are the centres of the fine sub-bins."""
+    base = oracle.default_config(_lib=L, uv_mode=1)
+    NB, F = base.hough_bins, base.hough_fine
+    # half 1 range [-ty_in, ty_max]; the constructions use |t_y| of the track
+    lo = -base.hough_ty_in
+    w = (base.hough_ty_max + base.hough_ty_in) / NB
+    layers = UV_LAYERS
+    for seed in (401, 402, 403, 404):
+        # (a) edge straddle: alternate layers 0.1 bin below / above an edge
+        edge = lo + 11 * w
+        x, zone, lh, half = _stereo_event(seed, {L: edge + (0.1 if k % 2 else -0.1) * w
+                                                 for k, L in enumerate(layers)})
+        if half == 0:  # the mirrored range of half 0 puts the edge elsewhere
+            continue
+        r = oracle.seeding_event(base, x, zone, _lib=L)
+        assert len(r["seeds"]) == 1 and r["seeds"][0]["nuv"] == 6
+        assert [r["seeds"][0]["hits"][q] for q in layers] == [lh[q] for q in layers]
+        # (b) layers, not hits: 4 true stereo layers at 0.05 against 2 layers
+        # holding 4 decoy hits each at 0.15; one cluster kept
+        one = oracle.default_config(_lib=L, uv_mode=1, hough_clusters=1)
+        spec = {L: 0.05 for L in layers}
+        spec[9] = spec[10] = None
+        x, zone, lh, half = _stereo_event(seed, spec, extra=[(9, 0.15)] * 4 + [(10, 0.15)] * 4)
+        r = oracle.seeding_event(one, x, zone, _lib=L)
+        assert len(r["seeds"]) == 1 and r["seeds"][0]["nuv"] == 4
+        assert [r["seeds"][0]["hits"][q] for q in (1, 2, 5, 6)] == [lh[q] for q in (1, 2, 5, 6)]
+        # (c) best first: the true 6-layer cluster against a 5-layer decoy
+        x, zone, lh, half = _stereo_event(seed, {L: 0.05 for L in layers},
+                                          extra=[(L, 0.15) for L in layers[:5]])
+        r = oracle.seeding_event(one, x, zone, _lib=L)
+        assert len(r["seeds"]) == 1 and r["seeds"][0]["nuv"] == 6
+        assert [r["seeds"][0]["hits"][q] for q in layers] == [lh[q] for q in layers]
+        # (d) hypothesis grid: t_y at a sub-bin centre, tolerance 1 um
+        ty = lo + w * (11 + 1.5 * 2.0 / F)
+        tight = oracle.default_config(_lib=L, uv_mode=1, uv_tol=1e-3)
+        x, zone, lh, half = _stereo_event(seed, {L: ty for L in layers})
+        r = oracle.seeding_event(tight, x, zone, _lib=L)
+        assert len(r["seeds"]) == 1 and r["seeds"][0]["nuv"] == 6
+        assert r["seeds"][0]["ty"] == pytest.approx(ty, rel=1e-9)
+        return
+    raise AssertionError("no upper-half track among the constructed events")
+
+
 ALL_CHECKS = (check_paper_constants, check_window_closed_forms, check_k3_chord,
               check_noise_free_recovery, check_triplets_brute_force, check_clone_kill_pairwise,
-              check_tolerance_boundaries, check_matching_grid)
+              check_tolerance_boundaries, check_matching_grid, check_hough_noise_free,
+              check_hough_clusters)
 
 
 # ---------------------------------------------------------------------------
@@ -403,6 +488,42 @@ def test_uv_recovers_true_stereo_hits(ocfg):
             assert sd["hits"][Lx] == tr["layer_hit"][0, Lx]
         assert sd["nuv"] == 6
         assert sd["ty"] == pytest.approx(tr["ty"][0], rel=1e-10, abs=1e-13)
+
+
+def test_hough_noise_free():
+    check_hough_noise_free()
+
+
+def test_hough_cluster_cases():
+    check_hough_clusters()
+
+
+def test_hough_similar_to_iterative():
+    """Section 3.4: the two UV approaches have similar tracking performance.
+    On the Run-3-like sample the Hough-cluster variant's efficiency above
+    5 GeV/c is within 1% of the iterative one's, with few ghosts."""
+    b = workload("run3", n_events=30)
+    eff = {}
+    for mode in (0, 1):
+        cfg = oracle.default_config(uv_mode=mode)
+        res = oracle.seeding_batch(cfg, b)
+        ntrue = nfound = nseed = nghost = 0
+        for e, r in enumerate(res):
+            tr = b.tracks_of(e)
+            seen = set()
+            for sd in r["seeds"]:
+                nseed += 1
+                t, pur = truth_track_of(b, e, sd["hits"])
+                if t < 0 or pur < 0.7:
+                    nghost += 1
+                else:
+                    seen.add(t)
+            good = (tr["p"] > 5.0) & ((tr["layer_hit"] >= 0).sum(1) >= 10)
+            ntrue += good.sum()
+            nfound += sum((b.trk_off[e] + k) in seen for k in np.nonzero(good)[0])
+        eff[mode] = nfound / ntrue
+        assert nghost / nseed < 0.02
+    assert abs(eff[1] - eff[0]) < 0.01, eff
 
 
 def test_synthetic_efficiency_targets(ocfg, zmx_calibrated):
