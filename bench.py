@@ -227,6 +227,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="batched measurement only (for profiling)")
     ap.add_argument("--no-autotune", action="store_true", help="paper defaults, no launch-shape tuning")
+    ap.add_argument("--no-variants", action="store_true", help="skip the Hough-cluster UV measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -353,6 +354,12 @@ def main():
     result["roofline"]["hbm"]["algorithmic_bytes"] = alg_bytes
     result["roofline"]["hbm"]["achieved_gbs"] = alg_bytes / (seed_ms / 1000.0) / 1e9 if seed_ms > 0 else 0.0
 
+    # ---------------- the Hough-cluster UV variant on the same batch
+    if not args.no_variants:
+        result["uv_hough"] = time_variant(st, dict(zmx=zmx, uv_mode=1, **tuned), db, out, cap, n_ev, flush,
+                                          stream, args.steps)
+        log(f"uv_hough: {result['uv_hough']}")
+
     if args.quick:
         graph.close()
         ctx.close()
@@ -461,6 +468,37 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def time_variant(st, overrides, db, out, cap, n_ev, flush, stream, steps):
+    """Batched graph replay of the same device batch under another method
+    configuration: events/s and per-kernel times."""
+    import torch
+    ctx = st.Context(st.st_config_default(**overrides), device=db.x.device.index or 0)
+    ctx.st_reserve(n_ev, n_ev * db.max_hits, db.max_hits, cap)
+    ctx.st_set_timing(True)
+    g = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
+    kms = {}
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            g.st_graph_launch(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(steps):
+            flush.fill_(1)
+            e0.record(stream)
+            g.st_graph_launch(stream)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+            for k, v in ctx.st_kernel_ms().items():
+                kms[k] = kms.get(k, 0.0) + v / steps
+    seeds = int(out.ev_off[-1].item())
+    g.close()
+    ctx.close()
+    return {"value": n_ev * steps / (tot / 1000.0), "unit": "events/s", "ms_per_step": tot / steps,
+            "kernel_ms": kms, "seeds_per_event": seeds / n_ev,
+            "config": {k: v for k, v in overrides.items() if k != "zmx"}}
 
 
 def poll_grow(st, ctx, ticket, n_events, timeout_us=60_000_000):

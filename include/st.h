@@ -100,6 +100,14 @@ typedef struct {
     int32_t smem_hits;         /* hits of one detector half staged in shared memory */
     int32_t cand_cap;          /* x-z candidates per (event, half) work item */
     int32_t pad2;
+    /* UV seeding, Hough-cluster variant (Section 3.4, second approach; bin
+     * counts and ranges are not given in the paper) */
+    int32_t uv_mode;           /* 0: iterative over an initial layer (default), 1: Hough clusters */
+    int32_t hough_bins;        /* coarse t_y bins (2..64); a cluster is two adjacent bins */
+    int32_t hough_fine;        /* t_y hypotheses per kept cluster, at sub-bin centres (1..8) */
+    int32_t hough_clusters;    /* clusters kept per seed, most populated first (1..8) */
+    double hough_ty_max;       /* coarse t_y range [-hough_ty_in, hough_ty_max] for half 1, */
+    double hough_ty_in;        /* mirrored for half 0 */
 } st_config;
 
 /* Hits of a batch of events (CSR).  All arrays are DEVICE memory.

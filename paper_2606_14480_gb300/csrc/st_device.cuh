@@ -56,6 +56,12 @@ struct DevParams {
     float uv_tol;
     float uv_ylo[2], uv_yhi[2];  // first-layer y window per half
     float inv_sy2;
+    // Hough-cluster UV variant
+    int uv_mode;
+    int h_bins, h_fine, h_clusters;
+    float h_lo[2];         // lower edge of the coarse t_y range per half
+    float h_w, h_inv_w;    // coarse bin width and its inverse
+    float h_step;          // sub-bin width in coarse-bin units (2 / h_fine)
     // seed state
     float zS, zbS, fS, dfS;
     // matching

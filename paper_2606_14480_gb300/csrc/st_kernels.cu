@@ -360,6 +360,86 @@ __device__ void uv_chain(const DevParams& P, const float* X, const int* szl, con
     o.tyr = ty;
 }
 
+// Hough-cluster variant (Section 3.4, second approach), step 1 for one seed:
+// every stereo hit of the half whose y lies in the first-layer window goes to
+// coarse bin floor((y/z - lo) / w) of its layer's 64-bit occupancy mask; a
+// cluster b is bins (b, b+1), its population the number of layers with a hit
+// in it, counted for all clusters at once with three bit planes.  The kept
+// clusters (most populated first, at least n_uv_min, ties to the smaller b)
+// go to out[]; returns how many.
+__device__ int hough_select(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
+                            const float* Xs, int h, uint8_t* out) {
+    ull s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+        const float Xl = Xs[u], t = P.ut[u];
+        const float xa = fmaf(-P.uv_yhi[h], t, Xl), xb = fmaf(-P.uv_ylo[h], t, Xl);
+        const int st = szl[6 + u], n = szl[7 + u] - st;
+        const uint16_t* lz = lut + (6 + u) * kLutBins;
+        const int lo = zlo(X + st, lz, n, fminf(xa, xb)), hi = zhi(X + st, lz, n, fmaxf(xa, xb));
+        ull m = 0;
+        for (int k = lo; k < hi; ++k) {
+            const float ty = (Xl - X[st + k]) * P.uinv_t[u] * P.uinv_z[u];
+            const int b = min(max(__float2int_rd((ty - P.h_lo[h]) * P.h_inv_w), 0), P.h_bins - 1);
+            m |= 1ull << b;
+        }
+        const ull c = m | (m >> 1);  // bit b: a hit in bin b or b + 1
+        const ull c0 = s0 & c;
+        s0 ^= c;
+        const ull c1 = s1 & c0;
+        s1 ^= c0;
+        s2 |= c1;
+    }
+    const ull valid = ~0ull >> (65 - P.h_bins);  // clusters 0 .. bins-2
+    int ns = 0;
+    for (int p = 6; p >= P.n_uv_min && ns < P.h_clusters; --p) {
+        ull e = valid & ((p & 1) ? s0 : ~s0) & ((p & 2) ? s1 : ~s1) & ((p & 4) ? s2 : ~s2);
+        while (e && ns < P.h_clusters) {
+            out[ns++] = static_cast<uint8_t>(__ffsll(static_cast<long long>(e)) - 1);
+            e &= e - 1;
+        }
+    }
+    return ns;
+}
+
+// step 2 for one t_y hypothesis: the closest hit within uv_tol in every
+// stereo layer (ties to the smaller x); stops once n_uv_min is out of reach.
+__device__ void uv_hough(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
+                         const float* Xs, float ty, UV& o) {
+    int n = 0;
+    o.n = 0;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+        const float xp = Xs[u] - P.ut[u] * ty * P.uz[u];
+        const int st = szl[6 + u], nn = szl[7 + u] - st;
+        const float* xs = X + st;
+        int k = zlo(xs, lut + (6 + u) * kLutBins, nn, xp - P.uv_tol);
+        int best = -1;
+        float bd = 0.f;
+        for (; k < nn; ++k) {
+            const float xh = xs[k];
+            if (xh > xp + P.uv_tol) break;
+            const float d = fabsf(xh - xp);
+            if (d <= P.uv_tol && (best < 0 || d < bd)) {
+                best = st + k;
+                bd = d;
+            }
+        }
+        o.pos[u] = best;
+        n += best >= 0;
+        if (n + (5 - u) < P.n_uv_min) {
+            o.n = n;
+            return;
+        }
+    }
+    o.n = n;
+    o.tyr = ty;
+}
+
+__device__ __forceinline__ float hough_ty(const DevParams& P, int h, int b, int f) {
+    return fmaf(P.h_w, static_cast<float>(b) + (static_cast<float>(f) + 0.5f) * P.h_step, P.h_lo[h]);
+}
+
 // Straight-line fit y = y0 + ty z of a complete chain (o.pos, o.n, o.tyr).
 // The y of each hit is formed as a float-float from error-free
 // transformations and fitted relative to the line y = tyr z, so chi2_y keeps
@@ -464,7 +544,7 @@ size_t seed_slot_bytes(int cand_cap, int max_xhits) {
     return align16(sizeof(int) * 16 * size_t(cand_cap)) +
            sizeof(ull) * (size_t(max_xhits) + cand_cap + size_t(kTripPerCand) * cand_cap) +
            16 + (2 * sizeof(uint4) + sizeof(uint2)) * kUvStore + sizeof(float) * 6 * size_t(cand_cap) + 8 +
-           sizeof(ull) * kTripLocal * kMaxThreads;
+           sizeof(ull) * kTripLocal * kMaxThreads + 9 * size_t(cand_cap);
 }
 
 // Two instantiations: CTAs of up to 256 threads with five per SM (48
@@ -520,6 +600,8 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     uint2* vmeta = reinterpret_cast<uint2*>(vfit + kUvStore);      // (seed, pass | initial hit << 1)
     float* g_xs = reinterpret_cast<float*>(vmeta + kUvStore);
     ull* tloc = reinterpret_cast<ull*>(g_xs + 6 * CC) + tid * kTripLocal;  // this thread's triplet buffer
+    uint8_t* hcl = reinterpret_cast<uint8_t*>(reinterpret_cast<ull*>(g_xs + 6 * CC) + kTripLocal * kMaxThreads);
+    uint8_t* hn = hcl + 8 * CC;  // Hough variant: kept clusters per seed and their count
     __shared__ int s_nvalid;
     int spar = 0;  // which half of tmp the next block scan uses
 
@@ -748,13 +830,21 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
         }
         if (tid == 0) s_nvalid = 0;
         __syncthreads();
-        // chains are numbered pass-major (all pass A chains, then pass B) so
-        // that a warp's chains mostly share their initial layer
-        const int nuv = 2 * nk;
+        const bool hough = P.uv_mode == 1;
+        if (hough) {
+            for (int j = tid; j < nk; j += T) hn[j] = static_cast<uint8_t>(hough_select(P, X, szl, lut, Xs + 6 * j, h, hcl + 8 * j));
+            __syncthreads();
+        }
+        // iterative: one item per (seed, pass), numbered pass-major (all pass
+        // A chains, then pass B) so that a warp's chains mostly share their
+        // initial layer; Hough: one item per seed with its hypotheses
+        const int nuv = hough ? nk : 2 * nk;
         for (int b = 0; b < nuv; b += T) {
             const int i = b + tid;
             int cntc = 0, lo = 0;
-            if (i < nuv) {
+            if (i < nuv && hough) {
+                cntc = hn[i] * P.h_fine;
+            } else if (i < nuv) {
                 const int pass = i >= nk, j = i - (pass ? nk : 0);
                 const int ui = P.uv_init[pass];
                 const float Xi = Xs[6 * j + ui];
@@ -785,9 +875,14 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                         kinit = sA[o];
                     }
                     const int i2 = sB[o];
-                    const int pass = i2 >= nk, j = i2 - (pass ? nk : 0);
+                    const int pass = hough ? 0 : i2 >= nk, j = i2 - (pass ? nk : 0);
                     UV u;
-                    uv_chain(P, X, szl, lut, Xs + 6 * j, pass, kinit, u);
+                    if (hough) {
+                        const int r = kinit / P.h_fine;
+                        uv_hough(P, X, szl, lut, Xs + 6 * j, hough_ty(P, h, hcl[8 * j + r], kinit - r * P.h_fine), u);
+                    } else {
+                        uv_chain(P, X, szl, lut, Xs + 6 * j, pass, kinit, u);
+                    }
                     if (u.n >= P.n_uv_min) {
                         ++ctr[6];
                         const int sidx = atomicAdd(&s_nvalid, 1);
@@ -890,8 +985,13 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     u.wm = f.z;
                     u.zm = f.w;
                 } else {
-                    uv_chain(P, X, szl, lut, Xs + 6 * j, static_cast<int>((key >> 29) & 1),
-                             static_cast<int>((key >> 13) & 0xFFFFu), u);
+                    const int kinit = static_cast<int>((key >> 13) & 0xFFFFu);
+                    if (P.uv_mode == 1) {
+                        const int r = kinit / P.h_fine;
+                        uv_hough(P, X, szl, lut, Xs + 6 * j, hough_ty(P, h, hcl[8 * j + r], kinit - r * P.h_fine), u);
+                    } else {
+                        uv_chain(P, X, szl, lut, Xs + 6 * j, static_cast<int>((key >> 29) & 1), kinit, u);
+                    }
                     uv_fit(P, X, th, dth, u);
                 }
                 int32_t* ho = A.pool_hits + r * 12;

@@ -138,6 +138,12 @@ extern "C" void st_config_default(st_config* c) {
     c->tol_ty = 1.0 / 937.5;
     c->chi2_match_max = 2.0;
     c->velo_unique = 0;
+    c->uv_mode = 0;
+    c->hough_bins = 64;
+    c->hough_fine = 4;
+    c->hough_clusters = 8;  // "up to eight of the best bins"
+    c->hough_ty_max = 0.33;
+    c->hough_ty_in = 0.01;
     c->threads_seed = 256;
     c->threads_build = 512;
     c->threads_match = 256;
@@ -162,6 +168,10 @@ bool derive_params(const st_config& c, DevParams& P, std::string& err) {
     if (!(c.p_min > 0) || !(c.sigma_x > 0) || !(c.sigma_y > 0) || !(c.ext_tol > 0) || !(c.uv_tol > 0))
         return fail("p_min, sigma_x, sigma_y, ext_tol and uv_tol must be positive");
     if (c.n_uv_min < 2 || c.n_uv_min > 6) return fail("n_uv_min must be in [2, 6]");
+    if (c.uv_mode < 0 || c.uv_mode > 1) return fail("uv_mode must be 0 or 1");
+    if (c.hough_bins < 2 || c.hough_bins > 64 || c.hough_fine < 1 || c.hough_fine > 8 || c.hough_clusters < 1 ||
+        c.hough_clusters > 8 || !(c.hough_ty_max + c.hough_ty_in > 0))
+        return fail("Hough parameters: bins in [2, 64], fine and clusters in [1, 8], non-empty t_y range");
     if (!(c.invp_b != 0.0) || !(c.invp_a * c.invp_a + 4 * c.invp_b / c.p_min >= 0))
         return fail("Eq. invp parameters give no momentum limit");
     if (c.threads_seed < 64 || c.threads_seed > kMaxThreads || c.threads_seed % 32 ||
@@ -272,6 +282,18 @@ bool derive_params(const st_config& c, DevParams& P, std::string& err) {
     P.uv_ylo[1] = static_cast<float>(-c.uv_y_overlap);
     P.uv_yhi[1] = static_cast<float>(c.uv_y_max);
     P.inv_sy2 = static_cast<float>(1.0 / (c.sigma_y * c.sigma_y));
+    P.uv_mode = c.uv_mode;
+    P.h_bins = c.hough_bins;
+    P.h_fine = c.hough_fine;
+    P.h_clusters = c.hough_clusters;
+    {
+        const double w = (c.hough_ty_max + c.hough_ty_in) / c.hough_bins;
+        P.h_lo[0] = static_cast<float>(-c.hough_ty_max);
+        P.h_lo[1] = static_cast<float>(-c.hough_ty_in);
+        P.h_w = static_cast<float>(w);
+        P.h_inv_w = static_cast<float>(1.0 / w);
+        P.h_step = static_cast<float>(2.0 / c.hough_fine);
+    }
     {
         const double zb = c.z_state - c.z_ref;
         P.zS = static_cast<float>(c.z_state);

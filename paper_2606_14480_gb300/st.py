@@ -39,6 +39,8 @@ class StConfig(C.Structure):
         ("threads_seed", C.c_int32), ("threads_build", C.c_int32), ("threads_match", C.c_int32),
         ("ctas_per_sm", C.c_int32), ("smem_hits", C.c_int32), ("cand_cap", C.c_int32),
         ("pad2", C.c_int32),
+        ("uv_mode", C.c_int32), ("hough_bins", C.c_int32), ("hough_fine", C.c_int32),
+        ("hough_clusters", C.c_int32), ("hough_ty_max", C.c_double), ("hough_ty_in", C.c_double),
     ]
 
 
