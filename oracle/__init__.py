@@ -59,6 +59,7 @@ class OrConfig(C.Structure):
         ("chi2_match_max", C.c_double), ("velo_unique", C.c_int32), ("pad2", C.c_int32),
         ("uv_mode", C.c_int32), ("hough_bins", C.c_int32), ("hough_fine", C.c_int32),
         ("hough_clusters", C.c_int32), ("hough_ty_max", C.c_double), ("hough_ty_in", C.c_double),
+        ("final_sel", C.c_int32), ("pad3", C.c_int32), ("ghost_max", C.c_double), ("clone_margin", C.c_double),
     ]
 
 
@@ -84,7 +85,8 @@ class OrCounters(C.Structure):
 
 LEDGER_KINDS = {1: "pair_win", 2: "trip_win", 3: "ext_tol", 4: "ext_tie", 5: "chi2x", 6: "clone",
                 7: "uv_win", 8: "uv_tol", 9: "uv_tie", 10: "uv_sel", 11: "m_presel", 12: "m_chi2",
-                13: "m_tie", 14: "hough_bin"}
+                13: "m_tie", 14: "hough_bin", 15: "ghost", 16: "m_clone"}
+GHOST_NN_SIZE = 337
 
 _P = C.c_void_p
 
@@ -120,6 +122,12 @@ def lib(path: Optional[str] = None):
                 C.POINTER(OrConfig), C.c_int32, _P, C.c_int32, _P, _P, _P,
                 _P, C.c_int32, C.POINTER(C.c_int32), C.c_double, C.POINTER(OrCounters)]
             L.or_matching_event.restype = C.c_int32
+            L.or_ghost_nn.argtypes = [_P, _P]
+            L.or_ghost_nn.restype = C.c_double
+            L.or_final_selection.argtypes = [
+                C.POINTER(OrConfig), C.c_int32, _P, C.c_int32, _P, _P, _P, _P, _P, _P,
+                _P, C.c_int32, C.POINTER(C.c_int32), C.c_double]
+            L.or_final_selection.restype = C.c_int32
             _libs[key] = L
     return _libs[key]
 
@@ -258,6 +266,45 @@ def matching_event(cfg: OrConfig, velo, seed_state, *, ledger_tau: Optional[floa
         break
     out = {"status": int(st), "velo_idx": vidx, "chi2": chi2,
            "counters": {k: int(getattr(cnt, k)) for k in COUNTER_NAMES}}
+    if ledger_tau is not None:
+        out["ledger"] = lbuf[: nl.value]
+    return out
+
+
+def ghost_nn(nn, features, _lib=None) -> float:
+    """The ghost network (Section 4.4) on one input vector of 8 features."""
+    L = _lib or lib()
+    nn = np.ascontiguousarray(nn, dtype=np.float32)
+    assert nn.shape == (GHOST_NN_SIZE,)
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    return float(L.or_ghost_nn(_ptr(nn), _ptr(f)))
+
+
+def final_selection(cfg: OrConfig, velo, seed_state, seed_nhits, nn, velo_idx, chi2, *,
+                    ledger_tau: Optional[float] = None, _lib=None):
+    """Section 4.4 on one event's matching result.  Returns dict(velo_idx
+    (after selection), ghost_prob, ledger?)."""
+    L = _lib or lib()
+    velo = np.ascontiguousarray(velo, dtype=np.float64).reshape(-1, 4)
+    ss = np.ascontiguousarray(seed_state, dtype=np.float64).reshape(-1, 4)
+    nh = np.ascontiguousarray(seed_nhits, dtype=np.int32)
+    nn = np.ascontiguousarray(nn, dtype=np.float32)
+    assert nn.shape == (GHOST_NN_SIZE,)
+    vidx = np.ascontiguousarray(velo_idx, dtype=np.int32).copy()
+    c2 = np.ascontiguousarray(chi2, dtype=np.float64)
+    gp = np.zeros(ss.shape[0], np.float64)
+    cap = 4096 if ledger_tau is not None else 0
+    while True:
+        lbuf = np.zeros(cap, LEDGER_DTYPE) if ledger_tau is not None else None
+        nl = C.c_int32()
+        st = L.or_final_selection(C.byref(cfg), velo.shape[0], _ptr(velo), ss.shape[0], _ptr(ss), _ptr(nh),
+                                  _ptr(nn), _ptr(vidx), _ptr(c2), _ptr(gp), _ptr(lbuf), cap, C.byref(nl),
+                                  float(ledger_tau) if ledger_tau is not None else -1.0)
+        if ledger_tau is not None and nl.value > cap:
+            cap = nl.value
+            continue
+        break
+    out = {"status": int(st), "velo_idx": vidx, "ghost_prob": gp}
     if ledger_tau is not None:
         out["ledger"] = lbuf[: nl.value]
     return out

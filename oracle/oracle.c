@@ -99,6 +99,9 @@ void or_config_default(or_config* c) {
     c->hough_clusters = 8;   /* "up to eight of the best bins" */
     c->hough_ty_max = 0.33;
     c->hough_ty_in = 0.01;
+    c->final_sel = 0;
+    c->ghost_max = 0.8;      /* Section 4.4 */
+    c->clone_margin = 0.05;
 }
 
 static int config_ok(const or_config* c) {
@@ -117,6 +120,7 @@ static int config_ok(const or_config* c) {
     if (c->hough_bins < 2 || c->hough_bins > 64 || c->hough_fine < 1 || c->hough_fine > 8 ||
         c->hough_clusters < 1 || c->hough_clusters > 8 || !(c->hough_ty_max + c->hough_ty_in > 0))
         return 0;
+    if (c->final_sel < 0 || c->final_sel > 1 || (c->final_sel && c->velo_unique)) return 0;
     return 1;
 }
 
@@ -1004,5 +1008,84 @@ int32_t or_matching_event(const or_config* c, int32_t n_velo, const double* velo
         counters->match_presel += E.cnt.match_presel;
         counters->matched += E.cnt.matched;
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Final selection, Section 4.4                                             */
+/* ------------------------------------------------------------------------ */
+
+double or_ghost_nn(const float* nn, const double f[8]) {
+    const float* mean = nn;
+    const float* inv_scale = nn + 8;
+    const float* W1 = nn + 16;
+    const float* b1 = nn + 16 + 256;
+    const float* w2 = nn + 16 + 256 + 32;
+    const double b2 = nn[16 + 256 + 64];
+    double in[8];
+    for (int i = 0; i < 8; ++i) in[i] = (f[i] - mean[i]) * inv_scale[i];
+    double z = b2;
+    for (int k = 0; k < 32; ++k) {
+        double a = b1[k];
+        for (int i = 0; i < 8; ++i) a += W1[8 * k + i] * in[i];
+        if (a > 0) z += w2[k] * a;
+    }
+    return 1.0 / (1.0 + exp(-z));
+}
+
+int32_t or_final_selection(const or_config* c, int32_t n_velo, const double* velo, int32_t n_seeds,
+                           const double* seed_state, const int32_t* seed_nhits, const float* nn,
+                           int32_t* velo_idx, const double* chi2, double* ghost_prob,
+                           or_ledger* ledger, int32_t ledger_cap, int32_t* n_ledger, double tau) {
+    ev_t E;
+    memset(&E, 0, sizeof(E));
+    E.c = c;
+    E.led = ledger;
+    E.led_cap = ledger ? ledger_cap : 0;
+    E.tau = (ledger || n_ledger) ? tau : -1.0;
+    if (n_ledger) *n_ledger = 0;
+    if (n_velo < 0 || n_seeds < 0 || !nn) return -1;
+    for (int s = 0; s < n_seeds; ++s) {
+        const int v = velo_idx[s];
+        ghost_prob[s] = 1.0;
+        if (v < 0 || v >= n_velo) continue;
+        const double xS = seed_state[4 * s + 0], yS = seed_state[4 * s + 1];
+        const double txS = seed_state[4 * s + 2], tyS = seed_state[4 * s + 3];
+        const double xV = velo[4 * v + 0], yV = velo[4 * v + 1];
+        const double txV = velo[4 * v + 2], tyV = velo[4 * v + 3];
+        const double dtx = txV - txS, dty = tyV - tyS;
+        const double zmx = c->zmx[0] + c->zmx[1] * fabs(dtx) + c->zmx[2] * dtx * dtx + c->zmx[3] * fabs(xS) +
+                           c->zmx[4] * txV * txV;
+        /* the two segments at z_match_x and z_match_y, as in the matching */
+        const double xv_m = xV + (zmx - c->z_velo) * txV, xs_m = xS + (zmx - c->z_state) * txS;
+        const double yv_m = yV + (c->z_match_y - c->z_velo) * tyV, ys_m = yS + (c->z_match_y - c->z_state) * tyS;
+        const double dx = xv_m - xs_m, dy = yv_m - ys_m;
+        /* pseudorapidity of the VELO segment: tan(theta) = |slope|, eta =
+         * -ln tan(theta/2) = asinh(1/|slope|); slopes below 1e-6 count as 1e-6 */
+        const double rho = fmax(sqrt(txV * txV + tyV * tyV), 1e-6);
+        const double f[8] = {zmx, dx, dy, dtx, dty, chi2[s], asinh(1.0 / rho), (double)seed_nhits[s]};
+        const double p = or_ghost_nn(nn, f);
+        ghost_prob[s] = p;
+        int32_t hh[2] = {s, v};
+        ledger_add(&E, OR_L_GHOST, 0, fabs(p - c->ghost_max) / c->ghost_max, hh, 2);
+        if (!(p < c->ghost_max)) velo_idx[s] = -1;
+    }
+    /* clone removal among the kept pairs: one pair per seed here, so only a
+     * shared VELO segment can make a clone */
+    int* drop = (int*)calloc((size_t)(n_seeds > 0 ? n_seeds : 1), sizeof(int));
+    for (int s = 0; s < n_seeds; ++s) {
+        if (velo_idx[s] < 0) continue;
+        for (int t = 0; t < n_seeds; ++t) {
+            if (t == s || velo_idx[t] != velo_idx[s]) continue;
+            const double d = ghost_prob[s] - ghost_prob[t];
+            int32_t hh[3] = {s, t, velo_idx[s]};
+            ledger_add(&E, OR_L_M_CLONE, 0, fabs(d - c->clone_margin) / c->clone_margin, hh, 3);
+            if (d >= c->clone_margin) drop[s] = 1;
+        }
+    }
+    for (int s = 0; s < n_seeds; ++s)
+        if (drop[s]) velo_idx[s] = -1;
+    free(drop);
+    if (n_ledger) *n_ledger = E.n_led;
     return 0;
 }

@@ -75,6 +75,11 @@ typedef struct {
     int32_t hough_clusters;       /* clusters kept per seed, best first (1..8) */
     double hough_ty_max;          /* coarse range [-hough_ty_in, hough_ty_max] for half 1, */
     double hough_ty_in;           /* mirrored for half 0 */
+    /* Matching final selection, Section 4.4 */
+    int32_t final_sel;            /* 1: ghost network, ghost_prob < ghost_max, clone removal */
+    int32_t pad3;
+    double ghost_max;             /* 0.8 */
+    double clone_margin;          /* 0.05 */
 } or_config;
 
 typedef struct {
@@ -97,7 +102,7 @@ enum {
     OR_L_PAIR_WIN = 1, OR_L_TRIP_WIN = 2, OR_L_EXT_TOL = 3, OR_L_EXT_TIE = 4,
     OR_L_CHI2X = 5, OR_L_CLONE = 6, OR_L_UV_WIN = 7, OR_L_UV_TOL = 8,
     OR_L_UV_TIE = 9, OR_L_UV_SEL = 10, OR_L_M_PRESEL = 11, OR_L_M_CHI2 = 12,
-    OR_L_M_TIE = 13, OR_L_HOUGH_BIN = 14
+    OR_L_M_TIE = 13, OR_L_HOUGH_BIN = 14, OR_L_GHOST = 15, OR_L_M_CLONE = 16
 };
 typedef struct {
     int32_t kind, half;
@@ -139,6 +144,27 @@ int32_t or_matching_event(const or_config* c, int32_t n_velo, const double* velo
                           int32_t* velo_idx, double* chi2,
                           or_ledger* ledger, int32_t ledger_cap, int32_t* n_ledger,
                           double tau, or_counters* counters);
+
+/* Ghost network of Section 4.4: 8 inputs, one hidden layer of 32 ReLU nodes,
+ * a sigmoid output.  Weight layout (float32, OR_GHOST_NN_SIZE values):
+ * mean[8], inv_scale[8] (inputs are standardised as (f - mean) * inv_scale),
+ * W1[32][8], b1[32], w2[32], b2.  Inputs, in the paper's order: z_match_x,
+ * dx, dy, dtx, dty, chi2_match, eta of the VELO segment, SciFi hits. */
+#define OR_GHOST_NN_SIZE 337
+double or_ghost_nn(const float* nn, const double f[8]);
+
+/* Final selection of the matched pairs of one event (Section 4.4), applied to
+ * the output of or_matching_event: for every seed with a match the eight
+ * inputs are formed from its VELO segment and seed state, the ghost
+ * probability is evaluated (ghost_prob[s]; 1 for seeds without a match),
+ * pairs with ghost_prob >= ghost_max are dropped, and a pair is dropped as a
+ * clone when another kept pair shares its VELO segment (or its seed) with a
+ * ghost probability lower by at least clone_margin.  velo_idx is updated in
+ * place (-1 = dropped).  seed_nhits: SciFi hits per seed. */
+int32_t or_final_selection(const or_config* c, int32_t n_velo, const double* velo, int32_t n_seeds,
+                           const double* seed_state, const int32_t* seed_nhits, const float* nn,
+                           int32_t* velo_idx, const double* chi2, double* ghost_prob,
+                           or_ledger* ledger, int32_t ledger_cap, int32_t* n_ledger, double tau);
 
 #ifdef __cplusplus
 }

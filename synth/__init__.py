@@ -12,6 +12,7 @@ from .events import (  # noqa: F401
     EventBatch,
     WORKLOADS,
     calibrate_zmatch,
+    ghost_nn_weights,
     make_events,
     make_workload,
 )

@@ -409,3 +409,21 @@ def calibrate_zmatch(z_state: float, *, det: Detector = DEFAULT_DETECTOR, n_trac
     A = np.stack([np.ones(ok.sum()), np.abs(dtx[ok]), dtx[ok] ** 2, np.abs(x_s[ok]), txv[ok] ** 2], axis=1)
     coef, *_ = np.linalg.lstsq(A, zint, rcond=None)
     return coef
+
+
+def ghost_nn_weights(seed: int = 1009) -> np.ndarray:
+    """Seeded stand-in weights for the ghost network of the matching's final
+    selection (8 inputs, 32 hidden nodes, 1 output; the trained weights are
+    not published).  Layout (float32, 337 values): input mean[8],
+    inverse scale[8], W1[32][8], b1[32], w2[32], b2.  The standardisation
+    constants are the rough centre and spread of each input on these
+    synthetic events, so the standardised inputs are of order one and the
+    output spreads over (0, 1)."""
+    rng = np.random.default_rng(seed)
+    mean = np.array([5200.0, 0.0, 0.0, 0.0, 0.0, 1.0, 2.0, 10.0])
+    scale = np.array([200.0, 10.0, 50.0, 0.1, 0.005, 1.0, 1.0, 1.0])
+    w1 = rng.normal(0.0, 1.0 / np.sqrt(8.0), (32, 8))
+    b1 = rng.normal(0.0, 0.3, 32)
+    w2 = rng.normal(0.0, 4.0 / np.sqrt(32.0), 32)
+    b2 = np.array([1.5])
+    return np.concatenate([mean, 1.0 / scale, w1.ravel(), b1, w2, b2]).astype(np.float32)

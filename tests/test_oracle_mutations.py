@@ -40,6 +40,13 @@ MUTATIONS = {
                        "const double ty = ty_lo + w * (sel[r] + f * 2.0 / F);"),
     "hough_y_sign": ("const double y = (XL - xh) / tL;\n            const double S = dmax2(dmax2(SL",
                      "const double y = (xh - XL) / tL;\n            const double S = dmax2(dmax2(SL"),
+    "nn_no_relu": ("        if (a > 0) z += w2[k] * a;", "        z += w2[k] * a;"),
+    "nn_standardise_sign": ("for (int i = 0; i < 8; ++i) in[i] = (f[i] - mean[i]) * inv_scale[i];",
+                            "for (int i = 0; i < 8; ++i) in[i] = (f[i] + mean[i]) * inv_scale[i];"),
+    "eta_inverted": ("asinh(1.0 / rho)", "asinh(rho)"),
+    "ghost_cut_reversed": ("if (!(p < c->ghost_max)) velo_idx[s] = -1;", "if (p < c->ghost_max) velo_idx[s] = -1;"),
+    "clone_margin_sign": ("if (d >= c->clone_margin) drop[s] = 1;", "if (-d >= c->clone_margin) drop[s] = 1;"),
+    "nn_hits_feature": ("chi2[s], asinh(1.0 / rho), (double)seed_nhits[s]};", "chi2[s], asinh(1.0 / rho), chi2[s]};"),
     "state_slope": ("s->tx_s = cd->th[1] + cd->th[2] * (2.0 * zb + 3.0 * c->d_ratio * zb * zb);",
                     "s->tx_s = cd->th[1];"),
 }

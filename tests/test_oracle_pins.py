@@ -399,10 +399,105 @@ def check_hough_clusters(L=None):
     raise AssertionError("no upper-half track among the constructed events")
 
 
+# ---------------------------------------------------------------------------
+# matching final selection (Section 4.4)
+# ---------------------------------------------------------------------------
+
+def _torch_mlp(nn, F):
+    """The 8-32-1 ghost network evaluated with torch's linear / relu /
+    sigmoid in float64 (a library statement of the same network)."""
+    import torch
+    w = torch.as_tensor(np.asarray(nn, np.float64))
+    mean, inv = w[:8], w[8:16]
+    W1, b1, w2, b2 = w[16:272].reshape(32, 8), w[272:304], w[304:336].reshape(1, 32), w[336:337]
+    x = (torch.as_tensor(np.asarray(F, np.float64)) - mean) * inv
+    h = torch.nn.functional.relu(torch.nn.functional.linear(x, W1, b1))
+    return torch.sigmoid(torch.nn.functional.linear(h, w2, b2))[:, 0].numpy()
+
+
+def _probe_weights(k, scale=1.0):
+    """Weights whose output is sigmoid(scale * f_k) for input k (two hidden
+    ReLU units carry +f_k and -f_k)."""
+    nn = np.zeros(337, np.float32)
+    nn[8:16] = 1.0
+    W1 = np.zeros((32, 8), np.float32)
+    W1[0, k], W1[1, k] = scale, -scale
+    nn[16:272] = W1.ravel()
+    nn[304], nn[305] = 1.0, -1.0
+    return nn
+
+
+def check_final_selection(L=None, zmx=None, n_events=6):
+    """(1) The network equals torch's evaluation on random inputs; (2) each
+    of the eight inputs, read back through probe weights, equals its
+    definition (the vectorised matching quantities of Section 4, eta =
+    -ln tan(theta/2) with tan(theta) the VELO slope, the SciFi hit count);
+    (3) with the seeded stand-in weights the kept pairs follow the two rules
+    of Section 4.4 (ghost probability below 0.8; a pair sharing its VELO
+    segment with a pair whose probability is lower by at least 0.05 is
+    dropped), checked pair by pair."""
+    from synth import ghost_nn_weights
+    rng = np.random.default_rng(5)
+    nn = ghost_nn_weights()
+    F = np.column_stack([rng.normal(5200, 300, 64), rng.normal(0, 10, 64), rng.normal(0, 60, 64),
+                         rng.normal(0, 0.2, 64), rng.normal(0, 0.01, 64), rng.uniform(0, 2, 64),
+                         rng.uniform(1, 6, 64), rng.integers(9, 13, 64)])
+    got = np.array([oracle.ghost_nn(nn, f, _lib=L) for f in F])
+    assert np.allclose(got, _torch_mlp(nn, F), rtol=1e-12, atol=1e-15)
+    cfg = oracle.default_config(_lib=L, final_sel=1)
+    if zmx is not None:
+        oracle.apply(cfg, {"zmx": zmx})
+    b = workload("match_stress", n_events=n_events)
+    res = oracle.seeding_batch(cfg, b, _lib=L)
+    nshared = ndropped = 0
+    for e, r in enumerate(res):
+        s = r["seeds"]
+        st = np.stack([s["x_s"], s["y_s"], s["tx_s"], s["ty_s"]], 1)
+        velo = b.velo_of(e).astype(np.float64)
+        nh = (s["nx"] + s["nuv"]).astype(np.int32)
+        m = oracle.matching_event(cfg, velo, st, _lib=L)
+        vi = m["velo_idx"]
+        ok = vi >= 0
+        if not ok.any():
+            continue
+        # the inputs by definition
+        V, S = velo[vi[ok]], st[ok]
+        dtx, dty = V[:, 2] - S[:, 2], V[:, 3] - S[:, 3]
+        A, B, Cc, D, E = (cfg.zmx[k] for k in range(5))
+        zm = A + B * np.abs(dtx) + Cc * dtx ** 2 + D * np.abs(S[:, 0]) + E * V[:, 2] ** 2
+        dx = (V[:, 0] + (zm - cfg.z_velo) * V[:, 2]) - (S[:, 0] + (zm - cfg.z_state) * S[:, 2])
+        dy = (V[:, 1] + (cfg.z_match_y - cfg.z_velo) * V[:, 3]) - (S[:, 1] + (cfg.z_match_y - cfg.z_state) * S[:, 3])
+        theta = np.arctan(np.hypot(V[:, 2], V[:, 3]))
+        eta = -np.log(np.tan(theta / 2))
+        want = np.column_stack([zm, dx, dy, dtx, dty, m["chi2"][ok], eta, nh[ok]])
+        for k, sc in enumerate((2.0 ** -10, 0.125, 2.0 ** -6, 1.0, 8.0, 1.0, 0.25, 0.125)):  # exact in float32
+            f = oracle.final_selection(cfg, velo, st, nh, _probe_weights(k, sc), vi, m["chi2"], _lib=L)
+            p = f["ghost_prob"][ok]
+            assert np.allclose(np.log(p / (1 - p)) / sc, want[:, k], rtol=1e-9, atol=1e-9), k
+        # the selection rules with the stand-in weights
+        f = oracle.final_selection(cfg, velo, st, nh, nn, vi, m["chi2"], _lib=L)
+        p = _torch_mlp(nn, want)
+        assert np.allclose(f["ghost_prob"][ok], p, rtol=1e-12, atol=1e-15)
+        idx = np.nonzero(ok)[0]
+        kept = {int(i): int(vi[i]) for i, pi in zip(idx, p) if pi < cfg.ghost_max}
+        pp = dict(zip(idx.tolist(), p.tolist()))
+        expect = np.full(len(vi), -1, np.int32)
+        for i, v in kept.items():
+            others = [j for j, w in kept.items() if w == v and j != i]
+            nshared += bool(others)
+            if all(pp[i] - pp[j] < cfg.clone_margin for j in others):
+                expect[i] = v
+            else:
+                ndropped += 1
+        assert np.array_equal(f["velo_idx"], expect)
+        assert np.all(f["ghost_prob"][~ok] == 1.0)
+    assert nshared > 0 and ndropped > 0
+
+
 ALL_CHECKS = (check_paper_constants, check_window_closed_forms, check_k3_chord,
               check_noise_free_recovery, check_triplets_brute_force, check_clone_kill_pairwise,
               check_tolerance_boundaries, check_matching_grid, check_hough_noise_free,
-              check_hough_clusters)
+              check_hough_clusters, check_final_selection)
 
 
 # ---------------------------------------------------------------------------
@@ -488,6 +583,10 @@ def test_uv_recovers_true_stereo_hits(ocfg):
             assert sd["hits"][Lx] == tr["layer_hit"][0, Lx]
         assert sd["nuv"] == 6
         assert sd["ty"] == pytest.approx(tr["ty"][0], rel=1e-10, abs=1e-13)
+
+
+def test_final_selection(zmx_calibrated):
+    check_final_selection(zmx=zmx_calibrated)
 
 
 def test_hough_noise_free():
