@@ -108,6 +108,11 @@ typedef struct {
     int32_t hough_clusters;    /* clusters kept per seed, most populated first (1..8) */
     double hough_ty_max;       /* coarse t_y range [-hough_ty_in, hough_ty_max] for half 1, */
     double hough_ty_in;        /* mirrored for half 0 */
+    /* Matching final selection (Section 4.4): ghost network, cut, clone removal */
+    int32_t final_sel;         /* 1: apply it in matching_run (weights from st_set_ghost_nn) */
+    int32_t pad3;
+    double ghost_max;          /* keep pairs with ghost probability below 0.8 */
+    double clone_margin;       /* drop a pair sharing a segment with one at least 0.05 less ghost-like */
 } st_config;
 
 /* Hits of a batch of events (CSR).  All arrays are DEVICE memory.
@@ -155,13 +160,17 @@ typedef struct {
 } st_velo;
 
 /* Matching output, one entry per seed (same indexing as st_seeds), DEVICE:
- *   velo_idx [cap] int32: event-local VELO index of the Long track, -1 = none
- *   chi2     [cap] float: chi2_match of that pair (0 if none)
- *   n_long   [n_events] int32 (may be NULL): Long tracks per event */
+ *   velo_idx   [cap] int32: event-local VELO index of the Long track, -1 = none
+ *   chi2       [cap] float: chi2_match of that pair (0 if none)
+ *   n_long     [n_events] int32 (may be NULL): Long tracks per event
+ *   ghost_prob [cap] float: with final_sel (required then; may be NULL
+ *              otherwise) the ghost network's output for the seed's best
+ *              pair, 1 if the seed had none */
 typedef struct {
     int32_t* velo_idx;
     float* chi2;
     int32_t* n_long;
+    float* ghost_prob;
 } st_long;
 
 /* Per-stage work counters, summed over the calls since the last reset. */
@@ -216,11 +225,27 @@ int seeding_run(st_ctx* ctx, const st_hits* hits, st_seeds* seeds, void* cuda_st
  * (Eq. z_match) and to z_match_y; pairs passing the preselection (Section
  * 4.2) get chi2_match; the seed's Long track is the pair with the lowest
  * chi2_match below chi2_match_max (ties: lower VELO index).  `seeds` must be
- * a seeding_run output for the same events (velo->n_events events).  The
- * UT-hit search and the ghost network of Sections 4.3-4.4 are not part of
- * this call.  Errors as seeding_run. */
+ * a seeding_run output for the same events (velo->n_events events).  With
+ * cfg.final_sel = 1 the final selection of Section 4.4 follows: the ghost
+ * network (weights from st_set_ghost_nn) evaluates every best pair from its
+ * z_match_x, dx, dy, dtx, dty, chi2_match, the VELO segment's pseudorapidity
+ * and the seed's SciFi hit count; pairs with a ghost probability >= ghost_max
+ * are dropped, and a pair sharing its VELO segment with a kept pair whose
+ * ghost probability is lower by >= clone_margin is dropped as a clone
+ * (velo_idx = -1, chi2 = 0).  ST_ESTATE if final_sel is set and no weights
+ * were given.  The UT-hit search of Section 4.3 is not part of this call.
+ * Errors as seeding_run. */
 int matching_run(st_ctx* ctx, const st_velo* velo, const st_seeds* seeds, st_long* out,
                  void* cuda_stream);
+
+/* Weights of the ghost network (Section 4.4): ST_GHOST_NN_SIZE floats, HOST
+ * memory, copied.  Layout: input mean[8] and inverse scale[8] (each input is
+ * standardised as (f - mean) * inv_scale), W1[32][8], b1[32] (hidden layer,
+ * ReLU), w2[32], b2 (output, sigmoid).  The trained weights of the paper are
+ * not published; any set may be given.  Call before the matching work that
+ * should use it.  ST_EINVAL for a wrong size or a non-finite value. */
+#define ST_GHOST_NN_SIZE 337
+int st_set_ghost_nn(st_ctx* ctx, const float* weights, int32_t n);
 
 /* Capture seeding_run + matching_run for these exact buffers and sizes into a
  * CUDA graph (persistent, work-queue kernels).  Scratch must be reserved
@@ -322,8 +347,9 @@ typedef struct {
 /* Wait up to timeout_us (0 = do not wait, < 0 = forever) for the batch of
  * `ticket`.  On ST_OK its seeds and Long tracks are copied by DMA from the
  * device output ring into the HOST buffers host_seeds (cap, ev_off, hits,
- * params, state, n_hits, status) and host_long (velo_idx, chi2, n_long; may
- * be NULL), info (may be NULL) is filled, and the ticket is released.
+ * params, state, n_hits, status) and host_long (velo_idx, chi2, n_long,
+ * ghost_prob; each may be NULL, as may host_long), info (may be NULL) is
+ * filled, and the ticket is released.
  * ST_PENDING (timeout_us == 0) or ST_TIMEOUT if not ready; ST_OVERFLOW if
  * host_seeds->cap is too small (ticket kept); ST_EINVAL for an unknown
  * ticket. */

@@ -74,6 +74,10 @@ struct DevParams {
     float cut_x, cut_y, cut_tx, cut_ty;
     float tolx_a, tolx_b, toly_a, toly_b, inv_toltx, inv_tolty, chi2m_max;
     int velo_unique;
+    // final selection (Section 4.4): ghost network weights, cut, clone margin
+    int final_sel;
+    float ghost_max, clone_margin;
+    float nn[337];  // mean[8], inv_scale[8], W1[32][8], b1[32], w2[32], b2
     // per layer, for the optional z / dxdy input check
     float zl[12], tl[12];
     int slot_of_zone[24];

@@ -1135,6 +1135,54 @@ __device__ __forceinline__ int match_pair(const DevParams& P, float vxh, float v
     return 1;
 }
 
+// The eight inputs of the ghost network (Section 4.4) for one pair: z_match_x,
+// dx, dy, dtx, dty (formed like match_pair's), slot 5 left for chi2_match,
+// the VELO segment's pseudorapidity asinh(1/|slope|) (= -ln tan(theta/2)),
+// slot 7 left for the seed's hit count.
+__device__ void pair_features(const DevParams& P, const float* vs, const float* ss, float f[8]) {
+    const float x = vs[0], y = vs[1], tx = vs[2], ty = vs[3];
+    float p, pe, s, se;
+    two_prod(P.dAV_hi, tx, p, pe);
+    two_sum(x, p, s, se);
+    const float vxh = s, vxl = se + fmaf(P.dAV_lo, tx, pe);
+    two_prod(P.dMV_hi, ty, p, pe);
+    two_sum(y, p, s, se);
+    const float vyh = s, vyl = se + fmaf(P.dMV_lo, ty, pe);
+    const float xS = ss[0], yS = ss[1], txS = ss[2], tyS = ss[3];
+    float xh, xl, yh, yl;
+    two_prod(P.dAS_hi, txS, p, pe);
+    two_sum(xS, p, xh, xl);
+    xl += fmaf(P.dAS_lo, txS, pe);
+    two_prod(P.dMS_hi, tyS, p, pe);
+    two_sum(yS, p, yh, yl);
+    yl += fmaf(P.dMS_lo, tyS, pe);
+    const float dtx = tx - txS, dty = ty - tyS;
+    const float dz = fmaf(P.Bx, fabsf(dtx), fmaf(P.Cx, dtx * dtx, fmaf(P.Ex * tx, tx, P.Dx * fabsf(xS))));
+    f[0] = P.A_hi + (P.A_lo + dz);
+    f[1] = fmaf(dz, dtx, (vxh - xh) + (vxl - xl));
+    f[2] = (vyh - yh) + (vyl - yl);
+    f[3] = dtx;
+    f[4] = dty;
+    f[6] = asinhf(1.f / fmaxf(sqrtf(fmaf(tx, tx, ty * ty)), 1e-6f));
+}
+
+// The ghost network: standardised inputs, 32 ReLU nodes, sigmoid output.
+// Every lane reads the same weight at the same time (uniform constant reads).
+__device__ float ghost_nn(const DevParams& P, const float f[8]) {
+    float in[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) in[i] = (f[i] - P.nn[i]) * P.nn[8 + i];
+    float z = P.nn[336];
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+        float a = P.nn[272 + k];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a = fmaf(P.nn[16 + 8 * k + i], in[i], a);
+        if (a > 0.f) z = fmaf(P.nn[304 + k], a, z);
+    }
+    return 1.f / (1.f + expf(-z));
+}
+
 // One event per work item; one thread per seed.  The event's VELO segments
 // are staged in shared memory with their float-float extrapolations and
 // bucketed by ty, so a seed only visits the buckets its |dty| cut can reach
@@ -1279,6 +1327,51 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
                     if (vt != v) continue;
                     const float ct = A.chi2[s0 + t];
                     if (ct < c || (ct == c && t < s)) {
+                        A.velo_idx[s0 + s] = -2 - v;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int s = tid; s < ns; s += T) {
+                if (A.velo_idx[s0 + s] <= -2) {
+                    A.velo_idx[s0 + s] = -1;
+                    A.chi2[s0 + s] = 0.f;
+                }
+            }
+            __syncthreads();
+        }
+        if (P.final_sel) {
+            // Section 4.4: ghost probability of each best pair and the cut
+            for (int s = tid; s < ns; s += T) {
+                const int v = A.velo_idx[s0 + s];
+                float p = 1.f;
+                if (v >= 0) {
+                    float f[8];
+                    pair_features(P, A.velo + (v0 + v) * 4, A.seed_state + (s0 + s) * 4, f);
+                    f[5] = A.chi2[s0 + s];
+                    f[7] = static_cast<float>(A.seed_n[2 * (s0 + s)] + A.seed_n[2 * (s0 + s) + 1]);
+                    p = ghost_nn(P, f);
+                    if (!(p < P.ghost_max)) {
+                        A.velo_idx[s0 + s] = -1;
+                        A.chi2[s0 + s] = 0.f;
+                    }
+                }
+                A.ghost_prob[s0 + s] = p;
+            }
+            __syncthreads();
+            // clones: a kept pair whose VELO segment another kept pair holds
+            // with a ghost probability lower by at least clone_margin (one
+            // pair per seed, so no two pairs share a seed); marked -2 - v
+            for (int s = tid; s < ns; s += T) {
+                const int v = A.velo_idx[s0 + s];
+                if (v < 0) continue;
+                const float p = A.ghost_prob[s0 + s];
+                for (int t = 0; t < ns; ++t) {
+                    if (t == s) continue;
+                    int vt = A.velo_idx[s0 + t];
+                    if (vt <= -2) vt = -2 - vt;
+                    if (vt == v && p - A.ghost_prob[s0 + t] >= P.clone_margin) {
                         A.velo_idx[s0 + s] = -2 - v;
                         break;
                     }

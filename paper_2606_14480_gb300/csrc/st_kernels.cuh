@@ -81,6 +81,8 @@ struct GatherArgs {
 
 struct MatchArgs {
     int64_t n_events;
+    const int8_t* seed_n;  // (nx, nuv) per seed
+    float* ghost_prob;     // per seed (final selection)
     const int64_t* velo_off;
     const float* velo;
     const int32_t* seed_off;

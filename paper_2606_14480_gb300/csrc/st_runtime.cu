@@ -144,6 +144,9 @@ extern "C" void st_config_default(st_config* c) {
     c->hough_clusters = 8;  // "up to eight of the best bins"
     c->hough_ty_max = 0.33;
     c->hough_ty_in = 0.01;
+    c->final_sel = 0;
+    c->ghost_max = 0.8;     // Section 4.4
+    c->clone_margin = 0.05;
     c->threads_seed = 256;
     c->threads_build = 512;
     c->threads_match = 256;
@@ -172,6 +175,9 @@ bool derive_params(const st_config& c, DevParams& P, std::string& err) {
     if (c.hough_bins < 2 || c.hough_bins > 64 || c.hough_fine < 1 || c.hough_fine > 8 || c.hough_clusters < 1 ||
         c.hough_clusters > 8 || !(c.hough_ty_max + c.hough_ty_in > 0))
         return fail("Hough parameters: bins in [2, 64], fine and clusters in [1, 8], non-empty t_y range");
+    if (c.final_sel < 0 || c.final_sel > 1 || (c.final_sel && c.velo_unique) || !(c.ghost_max > 0) ||
+        !(c.clone_margin >= 0))
+        return fail("final_sel must be 0 or 1 and excludes velo_unique; ghost_max > 0, clone_margin >= 0");
     if (!(c.invp_b != 0.0) || !(c.invp_a * c.invp_a + 4 * c.invp_b / c.p_min >= 0))
         return fail("Eq. invp parameters give no momentum limit");
     if (c.threads_seed < 64 || c.threads_seed > kMaxThreads || c.threads_seed % 32 ||
@@ -326,6 +332,9 @@ bool derive_params(const st_config& c, DevParams& P, std::string& err) {
     P.inv_tolty = static_cast<float>(1.0 / (ts * c.tol_ty));
     P.chi2m_max = static_cast<float>(c.chi2_match_max);
     P.velo_unique = c.velo_unique ? 1 : 0;
+    P.final_sel = c.final_sel;
+    P.ghost_max = static_cast<float>(c.ghost_max);
+    P.clone_margin = static_cast<float>(c.clone_margin);
     for (int l = 0; l < 12; ++l) {
         P.zl[l] = static_cast<float>(c.z[l]);
         P.tl[l] = static_cast<float>(c.dxdy[l]);
@@ -383,6 +392,7 @@ struct st_ctx {
     Pipeline* pipe = nullptr;
     std::mutex pipe_mu;
     bool timing = false;
+    bool has_nn = false;  // ghost network weights given
     cudaEvent_t tev[4][2] = {};
     bool tused[4] = {};
 };
@@ -701,9 +711,15 @@ static int run_matching(st_ctx* ctx, Workspace& w, const st_velo& V, const st_se
     m.velo = V.state;
     m.seed_off = S.ev_off;
     m.seed_state = S.state;
+    if (ctx->cfg.final_sel && !ctx->has_nn)
+        return set_err(ctx, ST_ESTATE, "final_sel needs the ghost network weights (st_set_ghost_nn)");
+    if (ctx->cfg.final_sel && !L.ghost_prob)
+        return set_err(ctx, ST_EINVAL, "final_sel needs an st_long.ghost_prob array");
     m.velo_idx = L.velo_idx;
     m.chi2 = L.chi2;
     m.n_long = L.n_long;
+    m.seed_n = S.n_hits;
+    m.ghost_prob = L.ghost_prob;
     m.velo_smem = ctx->velo_smem;
     m.queue = w.queues + 2;
     m.counters = ctx->counters;
@@ -755,6 +771,17 @@ extern "C" int matching_run(st_ctx* ctx, const st_velo* velo, const st_seeds* se
         return set_err(ctx, ST_EINVAL, "matching_run: null seeds or output array");
     ST_CUDA(ctx, cudaSetDevice(ctx->device));
     return run_matching(ctx, ctx->ws, *velo, *seeds, *out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int st_set_ghost_nn(st_ctx* ctx, const float* weights, int32_t n) {
+    if (!ctx) return ST_EINVAL;
+    if (!weights || n != ST_GHOST_NN_SIZE)
+        return set_err(ctx, ST_EINVAL, "st_set_ghost_nn: expected %d weights", ST_GHOST_NN_SIZE);
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(weights[i])) return set_err(ctx, ST_EINVAL, "st_set_ghost_nn: weight %d not finite", i);
+    std::memcpy(ctx->P.nn, weights, sizeof(float) * ST_GHOST_NN_SIZE);
+    ctx->has_nn = true;
+    return ST_OK;
 }
 
 extern "C" int st_set_timing(st_ctx* ctx, int enable) {
@@ -919,7 +946,7 @@ struct OutBlock {
     int64_t events = 0, cap = 0;
     int refs = 0;
     int32_t *ev_off, *status, *n_long, *hits, *vidx;
-    float *params, *state, *chi2;
+    float *params, *state, *chi2, *gp;
     int8_t* n;
 };
 
@@ -985,7 +1012,7 @@ static int64_t out_cap_for(int64_t hits) { return std::max<int64_t>(1024, hits /
 
 static size_t out_block_bytes(int64_t events, int64_t cap) {
     return al256(4 * size_t(events + 1)) + 2 * al256(4 * size_t(events)) + al256(48 * size_t(cap)) +
-           al256(32 * size_t(cap)) + al256(16 * size_t(cap)) + al256(2 * size_t(cap)) + 2 * al256(4 * size_t(cap));
+           al256(32 * size_t(cap)) + al256(16 * size_t(cap)) + al256(2 * size_t(cap)) + 3 * al256(4 * size_t(cap));
 }
 
 static void carve_out(OutBlock& o, char* p) {
@@ -1004,6 +1031,7 @@ static void carve_out(OutBlock& o, char* p) {
     o.n = reinterpret_cast<int8_t*>(take(2 * size_t(o.cap)));
     o.vidx = reinterpret_cast<int32_t*>(take(4 * size_t(o.cap)));
     o.chi2 = reinterpret_cast<float*>(take(4 * size_t(o.cap)));
+    o.gp = reinterpret_cast<float*>(take(4 * size_t(o.cap)));
 }
 
 static int slot_alloc(st_ctx* ctx, Slot& S, const st_pipeline_config& pc) {
@@ -1095,7 +1123,7 @@ static void launch_slot(st_ctx* ctx, Pipeline& pl, int si, std::unique_lock<std:
     st_hits H{ne, S.d_ev_off, pl.d_x, pl.d_zone, nullptr, nullptr, pl.pc.max_hits_per_event, 0};
     st_seeds Sd{ob->cap, ob->ev_off, ob->hits, ob->params, ob->state, ob->n, ob->status};
     st_velo V{ne, S.d_velo_off, pl.d_velo};
-    st_long L{ob->vidx, ob->chi2, ob->n_long};
+    st_long L{ob->vidx, ob->chi2, ob->n_long, ob->gp};
     if (rc == ST_OK) rc = run_seeding(ctx, S.ws, H, Sd, st, pl.pc.max_hits_per_slot, false);
     if (rc == ST_OK) rc = run_matching(ctx, S.ws, V, Sd, L, st);
     ck(cudaMemcpyAsync(S.h_counts, ob->ev_off, 4 * (ne + 1), cudaMemcpyDeviceToHost, st));
@@ -1405,6 +1433,7 @@ extern "C" int pipeline_poll(st_ctx* ctx, uint64_t ticket, st_seeds* hs, st_long
             if (hl->velo_idx) cp(hl->velo_idx, ob->vidx + s0, 4 * size_t(ns));
             if (hl->chi2) cp(hl->chi2, ob->chi2 + s0, 4 * size_t(ns));
             if (hl->n_long) cp(hl->n_long, ob->n_long + r->e0, 4 * size_t(n));
+            if (hl->ghost_prob) cp(hl->ghost_prob, ob->gp + s0, 4 * size_t(ns));
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }

@@ -41,6 +41,7 @@ class StConfig(C.Structure):
         ("pad2", C.c_int32),
         ("uv_mode", C.c_int32), ("hough_bins", C.c_int32), ("hough_fine", C.c_int32),
         ("hough_clusters", C.c_int32), ("hough_ty_max", C.c_double), ("hough_ty_in", C.c_double),
+        ("final_sel", C.c_int32), ("pad3", C.c_int32), ("ghost_max", C.c_double), ("clone_margin", C.c_double),
     ]
 
 
@@ -59,7 +60,7 @@ class StVelo(C.Structure):
 
 
 class StLong(C.Structure):
-    _fields_ = [("velo_idx", _P), ("chi2", _P), ("n_long", _P)]
+    _fields_ = [("velo_idx", _P), ("chi2", _P), ("n_long", _P), ("ghost_prob", _P)]
 
 
 COUNTER_NAMES = ("pairs", "triplets", "ext_ok", "cands", "kept", "uv_init", "uv_cands", "seeds",
@@ -101,6 +102,7 @@ SIGNATURES = {
     "st_graph_destroy": ([_P], None),
     "st_read_counters": ([_P, C.POINTER(StCounters), C.c_int], C.c_int),
     "st_set_timing": ([_P, C.c_int], C.c_int),
+    "st_set_ghost_nn": ([_P, _P, C.c_int32], C.c_int),
     "st_kernel_ms": ([_P, C.POINTER(C.c_float * 4)], C.c_int),
     "seeding_run_static": ([C.POINTER(StConfig), C.POINTER(StHits), C.POINTER(StSeeds), _P, C.c_char_p,
                             C.c_int32], C.c_int),
@@ -226,6 +228,10 @@ class Context:
                                              C.byref(out), C.byref(g)), "st_graph_create")
         return Graph(self, g)
 
+    def st_set_ghost_nn(self, weights):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        return self._check(self.lib.st_set_ghost_nn(self.h, w.ctypes.data, int(w.size)), "st_set_ghost_nn")
+
     def st_set_timing(self, enable=True):
         return self._check(self.lib.st_set_timing(self.h, int(enable)), "st_set_timing")
 
@@ -336,9 +342,10 @@ class DeviceOutputs:
         self.velo_idx = torch.zeros(max(cap, 1), dtype=torch.int32, device=dev)
         self.chi2 = torch.zeros(max(cap, 1), dtype=torch.float32, device=dev)
         self.n_long = torch.zeros(max(n_events, 1), dtype=torch.int32, device=dev)
+        self.ghost_prob = torch.zeros(max(cap, 1), dtype=torch.float32, device=dev)
         self.seeds = StSeeds(cap, _ptr(self.ev_off), _ptr(self.hits), _ptr(self.params), _ptr(self.state),
                              _ptr(self.n_hits), _ptr(self.status))
-        self.long = StLong(_ptr(self.velo_idx), _ptr(self.chi2), _ptr(self.n_long))
+        self.long = StLong(_ptr(self.velo_idx), _ptr(self.chi2), _ptr(self.n_long), _ptr(self.ghost_prob))
 
     def to_numpy(self) -> Dict[str, np.ndarray]:
         ev = self.ev_off.cpu().numpy()
@@ -347,7 +354,8 @@ class DeviceOutputs:
                 "state": self.state[:ns].cpu().numpy(), "n_hits": self.n_hits[:ns].cpu().numpy(),
                 "status": self.status[: len(ev) - 1].cpu().numpy(),
                 "velo_idx": self.velo_idx[:ns].cpu().numpy(), "chi2": self.chi2[:ns].cpu().numpy(),
-                "n_long": self.n_long[: len(ev) - 1].cpu().numpy()}
+                "n_long": self.n_long[: len(ev) - 1].cpu().numpy(),
+                "ghost_prob": self.ghost_prob[:ns].cpu().numpy()}
 
 
 class HostBuffers:
@@ -376,17 +384,19 @@ class HostBuffers:
         self.velo_idx = np.empty(max(cap, 1), np.int32)
         self.chi2 = np.empty(max(cap, 1), np.float32)
         self.n_long = np.zeros(max(n_events, 1), np.int32)
+        self.ghost_prob = np.empty(max(cap, 1), np.float32)
         p = lambda a: a.ctypes.data
         self.seeds = StSeeds(cap, p(self.ev_off), p(self.hits), p(self.params), p(self.state), p(self.n_hits),
                              p(self.status))
-        self.long = StLong(p(self.velo_idx), p(self.chi2), p(self.n_long))
+        self.long = StLong(p(self.velo_idx), p(self.chi2), p(self.n_long), p(self.ghost_prob))
 
     def to_numpy(self):
         ns = int(self.ev_off[-1])
         n = len(self.ev_off) - 1
         return {"ev_off": self.ev_off.copy(), "hits": self.hits[:ns].copy(), "params": self.params[:ns].copy(),
                 "state": self.state[:ns].copy(), "n_hits": self.n_hits[:ns].copy(), "status": self.status[:n].copy(),
-                "velo_idx": self.velo_idx[:ns].copy(), "chi2": self.chi2[:ns].copy(), "n_long": self.n_long[:n].copy()}
+                "velo_idx": self.velo_idx[:ns].copy(), "chi2": self.chi2[:ns].copy(), "n_long": self.n_long[:n].copy(),
+                "ghost_prob": self.ghost_prob[:ns].copy()}
 
 
 def seeding_run_static(cfg: StConfig, hits: StHits, seeds: StSeeds, stream=None) -> Tuple[int, str]:
