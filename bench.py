@@ -359,6 +359,11 @@ def main():
         result["uv_hough"] = time_variant(st, dict(zmx=zmx, uv_mode=1, **tuned), db, out, cap, n_ev, flush,
                                           stream, args.steps)
         log(f"uv_hough: {result['uv_hough']}")
+        from synth import ghost_nn_weights
+        result["final_selection"] = time_variant(st, dict(zmx=zmx, final_sel=1, **tuned), db, out, cap, n_ev,
+                                                 flush, stream, args.steps, nn=ghost_nn_weights())
+        result["final_selection"]["weights"] = "seeded stand-in (the trained weights are not published)"
+        log(f"final_selection: {result['final_selection']}")
 
     if args.quick:
         graph.close()
@@ -470,11 +475,13 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def time_variant(st, overrides, db, out, cap, n_ev, flush, stream, steps):
+def time_variant(st, overrides, db, out, cap, n_ev, flush, stream, steps, nn=None):
     """Batched graph replay of the same device batch under another method
     configuration: events/s and per-kernel times."""
     import torch
     ctx = st.Context(st.st_config_default(**overrides), device=db.x.device.index or 0)
+    if nn is not None:
+        ctx.st_set_ghost_nn(nn)
     ctx.st_reserve(n_ev, n_ev * db.max_hits, db.max_hits, cap)
     ctx.st_set_timing(True)
     g = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
