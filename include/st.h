@@ -112,7 +112,16 @@ typedef struct {
     int32_t final_sel;         /* 1: apply it in matching_run (weights from st_set_ghost_nn) */
     int32_t pad3;
     double ghost_max;          /* keep pairs with ghost probability below 0.8 */
-    double clone_margin;       /* drop a pair sharing a segment with one at least 0.05 less ghost-like */
+    double clone_margin;       /* drop a pair sharing a segment with one at least 0.05 less ghost-like (> 0) */
+    /* UT hits of the Long tracks (Section 4.3, ut_run) */
+    double ut_z[4];            /* UT layers UTaX, UTaU, UTbV, UTbX (not given in the paper) */
+    double ut_dxdy[4];         /* stereo slopes of the UT layers (x, u, v, x) */
+    double ut_gamma[2];        /* Eq. (gamma_parametrisation): A_gamma, B_gamma (per MeV) */
+    double ut_kick;            /* a pair's q/p = (tx_SciFi - tx_VELO) / ut_kick (MeV) */
+    double ut_loose[16];       /* per UT layer: A_L (mm), B_L (mm GeV/c), x_min, x_max; zeros = none */
+    double ut_tight[16];       /* per UT layer: A_T, B_T, x_min, x_max; zeros = none */
+    int32_t ut_min_hits;       /* Long tracks need this many UT hits in ut_run (0 = no requirement) */
+    int32_t pad4;
 } st_config;
 
 /* Hits of a batch of events (CSR).  All arrays are DEVICE memory.

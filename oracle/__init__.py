@@ -60,6 +60,9 @@ class OrConfig(C.Structure):
         ("uv_mode", C.c_int32), ("hough_bins", C.c_int32), ("hough_fine", C.c_int32),
         ("hough_clusters", C.c_int32), ("hough_ty_max", C.c_double), ("hough_ty_in", C.c_double),
         ("final_sel", C.c_int32), ("pad3", C.c_int32), ("ghost_max", C.c_double), ("clone_margin", C.c_double),
+        ("ut_z", C.c_double * 4), ("ut_dxdy", C.c_double * 4), ("ut_gamma", C.c_double * 2),
+        ("ut_kick", C.c_double), ("ut_loose", C.c_double * 16), ("ut_tight", C.c_double * 16),
+        ("ut_min_hits", C.c_int32), ("pad4", C.c_int32),
     ]
 
 
@@ -85,7 +88,7 @@ class OrCounters(C.Structure):
 
 LEDGER_KINDS = {1: "pair_win", 2: "trip_win", 3: "ext_tol", 4: "ext_tie", 5: "chi2x", 6: "clone",
                 7: "uv_win", 8: "uv_tol", 9: "uv_tie", 10: "uv_sel", 11: "m_presel", 12: "m_chi2",
-                13: "m_tie", 14: "hough_bin", 15: "ghost", 16: "m_clone"}
+                13: "m_tie", 14: "hough_bin", 15: "ghost", 16: "m_clone", 17: "ut_win", 18: "ut_tie"}
 GHOST_NN_SIZE = 337
 
 _P = C.c_void_p
@@ -128,6 +131,10 @@ def lib(path: Optional[str] = None):
                 C.POINTER(OrConfig), C.c_int32, _P, C.c_int32, _P, _P, _P, _P, _P, _P,
                 _P, C.c_int32, C.POINTER(C.c_int32), C.c_double]
             L.or_final_selection.restype = C.c_int32
+            L.or_ut_search.argtypes = [
+                C.POINTER(OrConfig), C.c_int32, _P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P, _P, _P,
+                _P, C.c_int32, C.POINTER(C.c_int32), C.c_double]
+            L.or_ut_search.restype = C.c_int32
             _libs[key] = L
     return _libs[key]
 
@@ -305,6 +312,37 @@ def final_selection(cfg: OrConfig, velo, seed_state, seed_nhits, nn, velo_idx, c
             continue
         break
     out = {"status": int(st), "velo_idx": vidx, "ghost_prob": gp}
+    if ledger_tau is not None:
+        out["ledger"] = lbuf[: nl.value]
+    return out
+
+
+def ut_search(cfg: OrConfig, velo, seed_state, velo_idx, ut_x, ut_layer, *, ledger_tau: Optional[float] = None,
+              _lib=None):
+    """Section 4.3 on one event's Long tracks.  Returns dict(ut_hits (n, 4),
+    n_ut, gamma, velo_idx (after the UT hit requirement), ledger?)."""
+    L = _lib or lib()
+    velo = np.ascontiguousarray(velo, dtype=np.float64).reshape(-1, 4)
+    ss = np.ascontiguousarray(seed_state, dtype=np.float64).reshape(-1, 4)
+    vidx = np.ascontiguousarray(velo_idx, dtype=np.int32).copy()
+    ux = np.ascontiguousarray(ut_x, dtype=np.float64)
+    ul = np.ascontiguousarray(ut_layer, dtype=np.int32)
+    ns = ss.shape[0]
+    hits = np.zeros((ns, 4), np.int32)
+    nut = np.zeros(ns, np.int32)
+    gam = np.zeros(ns, np.float64)
+    cap = 8192 if ledger_tau is not None else 0
+    while True:
+        lbuf = np.zeros(cap, LEDGER_DTYPE) if ledger_tau is not None else None
+        nl = C.c_int32()
+        st = L.or_ut_search(C.byref(cfg), velo.shape[0], _ptr(velo), ns, _ptr(ss), _ptr(vidx), len(ux), _ptr(ux),
+                            _ptr(ul), _ptr(hits), _ptr(nut), _ptr(gam), _ptr(lbuf), cap, C.byref(nl),
+                            float(ledger_tau) if ledger_tau is not None else -1.0)
+        if ledger_tau is not None and nl.value > cap:
+            cap = nl.value
+            continue
+        break
+    out = {"status": int(st), "ut_hits": hits, "n_ut": nut, "gamma": gam, "velo_idx": vidx}
     if ledger_tau is not None:
         out["ledger"] = lbuf[: nl.value]
     return out

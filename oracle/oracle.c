@@ -102,6 +102,24 @@ void or_config_default(or_config* c) {
     c->final_sel = 0;
     c->ghost_max = 0.8;      /* Section 4.4 */
     c->clone_margin = 0.05;
+    /* UT (Section 4.3): layer z not given in the paper (reading); x-u-v-x */
+    static const double uz[4] = {2327.5, 2372.5, 2597.5, 2642.5};
+    static const int us[4] = {0, 1, -1, 0};
+    for (int l = 0; l < 4; ++l) {
+        c->ut_z[l] = uz[l];
+        c->ut_dxdy[l] = us[l] * t5;
+    }
+    c->ut_gamma[0] = 7.707063e-11;  /* Table mag_params */
+    c->ut_gamma[1] = -7.817364e-3;
+    c->ut_kick = 1200.0;
+    /* Table ut_search_window_values: loose windows of UTaX, UTaU, UTbV */
+    static const double lw[16] = {0.8333, 3.3333, 1.2, 8.5, 0.8333, 3.3333, 1.2, 8.5,
+                                  1.3333, 3.3333, 1.5, 9.5, 0, 0, 0, 0};
+    /* tight windows of UTaU, UTbV, UTbX */
+    static const double tw[16] = {0, 0, 0, 0, 0.2, 0.6, 0.5, 2.0, 0.4, 1.2, 1.0, 4.0, 0.4, 1.2, 1.0, 4.0};
+    memcpy(c->ut_loose, lw, sizeof(lw));
+    memcpy(c->ut_tight, tw, sizeof(tw));
+    c->ut_min_hits = 3;      /* "more than two associated UT hits" */
 }
 
 static int config_ok(const or_config* c) {
@@ -120,7 +138,12 @@ static int config_ok(const or_config* c) {
     if (c->hough_bins < 2 || c->hough_bins > 64 || c->hough_fine < 1 || c->hough_fine > 8 ||
         c->hough_clusters < 1 || c->hough_clusters > 8 || !(c->hough_ty_max + c->hough_ty_in > 0))
         return 0;
-    if (c->final_sel < 0 || c->final_sel > 1 || (c->final_sel && c->velo_unique)) return 0;
+    if (c->final_sel < 0 || c->final_sel > 1 || (c->final_sel && c->velo_unique) || !(c->ghost_max > 0) ||
+        !(c->clone_margin > 0))
+        return 0;
+    if (c->ut_min_hits < 0 || c->ut_min_hits > 4 || !(c->ut_kick > 0)) return 0;
+    for (int l = 0; l < 4; ++l)
+        if (!(fabs(c->ut_z[l] - c->z_velo) > 0)) return 0;
     return 1;
 }
 
@@ -1044,7 +1067,7 @@ int32_t or_final_selection(const or_config* c, int32_t n_velo, const double* vel
     E.led_cap = ledger ? ledger_cap : 0;
     E.tau = (ledger || n_ledger) ? tau : -1.0;
     if (n_ledger) *n_ledger = 0;
-    if (n_velo < 0 || n_seeds < 0 || !nn) return -1;
+    if (!config_ok(c) || n_velo < 0 || n_seeds < 0 || !nn) return -1;
     for (int s = 0; s < n_seeds; ++s) {
         const int v = velo_idx[s];
         ghost_prob[s] = 1.0;
@@ -1086,6 +1109,83 @@ int32_t or_final_selection(const or_config* c, int32_t n_velo, const double* vel
     for (int s = 0; s < n_seeds; ++s)
         if (drop[s]) velo_idx[s] = -1;
     free(drop);
+    if (n_ledger) *n_ledger = E.n_led;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* UT hits of the Long tracks, Section 4.3                                  */
+/* ------------------------------------------------------------------------ */
+
+int32_t or_ut_search(const or_config* c, int32_t n_velo, const double* velo, int32_t n_seeds,
+                     const double* seed_state, int32_t* velo_idx, int32_t n_ut, const double* ut_x,
+                     const int32_t* ut_layer, int32_t* ut_hits, int32_t* n_ut_out, double* gamma,
+                     or_ledger* ledger, int32_t ledger_cap, int32_t* n_ledger, double tau) {
+    ev_t E;
+    memset(&E, 0, sizeof(E));
+    E.c = c;
+    E.led = ledger;
+    E.led_cap = ledger ? ledger_cap : 0;
+    E.tau = (ledger || n_ledger) ? tau : -1.0;
+    if (n_ledger) *n_ledger = 0;
+    if (!config_ok(c) || n_velo < 0 || n_seeds < 0 || n_ut < 0) return -1;
+    for (int i = 0; i < n_ut; ++i)
+        if (ut_layer[i] < 0 || ut_layer[i] > 3 || !isfinite(ut_x[i])) return -1;
+    for (int s = 0; s < n_seeds; ++s) {
+        for (int l = 0; l < 4; ++l) ut_hits[4 * s + l] = -1;
+        n_ut_out[s] = 0;
+        gamma[s] = 0.0;
+        const int v = velo_idx[s];
+        if (v < 0 || v >= n_velo) continue;
+        const double xV = velo[4 * v + 0], yV = velo[4 * v + 1];
+        const double txV = velo[4 * v + 2], tyV = velo[4 * v + 3];
+        const double txS = seed_state[4 * s + 2];
+        /* the pair's q/p from its kink, and 1/p in (GeV/c)^-1 for the windows */
+        const double qop = (txS - txV) / c->ut_kick;
+        const double inv_p_gev = 1000.0 * fabs(qop);
+        double g = c->ut_gamma[0] + c->ut_gamma[1] * qop; /* Eq. gamma_parametrisation */
+        int found = 0, n = 0;
+        for (int l = 0; l < 4; ++l) {
+            const double* w = found ? &c->ut_tight[4 * l] : &c->ut_loose[4 * l];
+            if (!(w[3] > 0)) continue; /* no window of this kind in this layer */
+            const double win = fmin(fmax(w[0] + w[1] * inv_p_gev, w[2]), w[3]);
+            const double dz = c->ut_z[l] - c->z_velo;
+            /* Eq. velo_ut_extrapolation, then the layer's measured coordinate */
+            const double xt = xV + txV * dz + g * dz * dz;
+            const double yt = yV + tyV * dz;
+            const double xm = xt - yt * c->ut_dxdy[l];
+            int best = -1;
+            double bd = INFINITY, bx = 0;
+            for (int i = 0; i < n_ut; ++i) {
+                if (ut_layer[i] != l) continue;
+                const double d = fabs(ut_x[i] - xm);
+                const double S = dmax2(dmax2(fabs(xm), fabs(ut_x[i])), 1.0);
+                int32_t hh[3] = {s, v, i};
+                ledger_add(&E, OR_L_UT_WIN, 0, fabs(d - win) / S, hh, 3);
+                if (d > win) continue;
+                if (best >= 0) {
+                    int32_t h2[4] = {s, v, best, i};
+                    ledger_add(&E, OR_L_UT_TIE, 0, fabs(d - bd) / S, h2, 4);
+                }
+                if (best < 0 || d < bd || (d == bd && (ut_x[i] < bx || (ut_x[i] == bx && i < best)))) {
+                    best = i;
+                    bd = d;
+                    bx = ut_x[i];
+                }
+            }
+            if (best < 0) continue;
+            ut_hits[4 * s + l] = best;
+            n++;
+            if (!found) {
+                /* gamma_x through the loose-window hit */
+                g = (ut_x[best] + yt * c->ut_dxdy[l] - xV - txV * dz) / (dz * dz);
+                found = 1;
+            }
+        }
+        n_ut_out[s] = n;
+        gamma[s] = g;
+        if (n < c->ut_min_hits) velo_idx[s] = -1;
+    }
     if (n_ledger) *n_ledger = E.n_led;
     return 0;
 }

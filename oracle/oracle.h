@@ -80,6 +80,15 @@ typedef struct {
     int32_t pad3;
     double ghost_max;             /* 0.8 */
     double clone_margin;          /* 0.05 */
+    /* UT hits of a Long track, Section 4.3 */
+    double ut_z[4];               /* UT layers UTaX, UTaU, UTbV, UTbX */
+    double ut_dxdy[4];            /* their stereo slopes (x, u, v, x) */
+    double ut_gamma[2];           /* Eq. gamma_parametrisation: A_gamma, B_gamma (per MeV) */
+    double ut_kick;               /* q/p of a pair = (tx_S - tx_V) / ut_kick (MeV) */
+    double ut_loose[16];          /* per layer A_L, B_L (mm GeV), x_min, x_max; zeros: no loose search */
+    double ut_tight[16];          /* per layer A_T, B_T, x_min, x_max; zeros: no tight search */
+    int32_t ut_min_hits;          /* keep Long tracks with at least this many UT hits (0: keep all) */
+    int32_t pad4;
 } or_config;
 
 typedef struct {
@@ -102,7 +111,8 @@ enum {
     OR_L_PAIR_WIN = 1, OR_L_TRIP_WIN = 2, OR_L_EXT_TOL = 3, OR_L_EXT_TIE = 4,
     OR_L_CHI2X = 5, OR_L_CLONE = 6, OR_L_UV_WIN = 7, OR_L_UV_TOL = 8,
     OR_L_UV_TIE = 9, OR_L_UV_SEL = 10, OR_L_M_PRESEL = 11, OR_L_M_CHI2 = 12,
-    OR_L_M_TIE = 13, OR_L_HOUGH_BIN = 14, OR_L_GHOST = 15, OR_L_M_CLONE = 16
+    OR_L_M_TIE = 13, OR_L_HOUGH_BIN = 14, OR_L_GHOST = 15, OR_L_M_CLONE = 16, OR_L_UT_WIN = 17,
+    OR_L_UT_TIE = 18
 };
 typedef struct {
     int32_t kind, half;
@@ -165,6 +175,22 @@ int32_t or_final_selection(const or_config* c, int32_t n_velo, const double* vel
                            const double* seed_state, const int32_t* seed_nhits, const float* nn,
                            int32_t* velo_idx, const double* chi2, double* ghost_prob,
                            or_ledger* ledger, int32_t ledger_cap, int32_t* n_ledger, double tau);
+
+/* UT hits of one event's Long tracks (Section 4.3).  For every seed with
+ * velo_idx[s] >= 0 the VELO segment is extrapolated with Eq.
+ * velo_ut_extrapolation, gamma_x from Eq. gamma_parametrisation at the pair's
+ * q/p, through the four UT layers in order.  Until a hit is found a layer is
+ * searched in its loose window, and the closest hit in it is attached and
+ * refits gamma_x through that hit; later layers are searched in their tight
+ * windows (closest hit attached).  Windows: min(max(A + B/p, x_min), x_max),
+ * p in GeV/c.  ut_x / ut_layer: the event's UT hits (measured x at y = 0,
+ * layer 0..3).  Outputs per seed: ut_hits[4] (event-local UT index, -1),
+ * n_ut, gamma (the final gamma_x); velo_idx is set to -1 where n_ut <
+ * ut_min_hits. */
+int32_t or_ut_search(const or_config* c, int32_t n_velo, const double* velo, int32_t n_seeds,
+                     const double* seed_state, int32_t* velo_idx, int32_t n_ut, const double* ut_x,
+                     const int32_t* ut_layer, int32_t* ut_hits, int32_t* n_ut_out, double* gamma,
+                     or_ledger* ledger, int32_t ledger_cap, int32_t* n_ledger, double tau);
 
 #ifdef __cplusplus
 }

@@ -1104,7 +1104,7 @@ constexpr int kTyBins = 64;
 constexpr float kTyRange = 0.32f;  // buckets of 0.01 over [-0.32, 0.32); outside values go to the end buckets
 
 size_t match_smem_bytes(int velo_smem) {
-    return sizeof(float) * 7 * size_t(velo_smem) + sizeof(int) * (size_t(velo_smem) + 2 * kTyBins + 8);
+    return sizeof(float) * 7 * size_t(velo_smem) + sizeof(int) * (2 * size_t(velo_smem) + 2 * kTyBins + 8);
 }
 
 __device__ __forceinline__ int ty_bin(float ty) {
@@ -1202,6 +1202,8 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
     int* bidx = reinterpret_cast<int*>(vit + VS);  // VELO indices grouped by ty bucket
     int* bcnt = bidx + VS;                         // [kTyBins]
     int* boff = bcnt + kTyBins;                    // [kTyBins + 1]
+    unsigned* vmin = reinterpret_cast<unsigned*>(boff + kTyBins + 8);  // final selection: lowest ghost
+                                                                       // probability per VELO segment
     __shared__ int s_item, s_cnt;
     ull ctr[3] = {0, 0, 0};
 
@@ -1362,18 +1364,36 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
             __syncthreads();
             // clones: a kept pair whose VELO segment another kept pair holds
             // with a ghost probability lower by at least clone_margin (one
-            // pair per seed, so no two pairs share a seed); marked -2 - v
-            for (int s = tid; s < ns; s += T) {
-                const int v = A.velo_idx[s0 + s];
-                if (v < 0) continue;
-                const float p = A.ghost_prob[s0 + s];
-                for (int t = 0; t < ns; ++t) {
-                    if (t == s) continue;
-                    int vt = A.velo_idx[s0 + t];
-                    if (vt <= -2) vt = -2 - vt;
-                    if (vt == v && p - A.ghost_prob[s0 + t] >= P.clone_margin) {
+            // pair per seed, so no two pairs share a seed); marked -2 - v.
+            // With clone_margin > 0 that is p - (lowest p on the segment) >=
+            // clone_margin; the lowest p per segment is an atomicMin of the
+            // probabilities' bits (non-negative floats order as unsigned).
+            if (nv <= VS) {
+                for (int v = tid; v < nv; v += T) vmin[v] = 0x7f800000u;
+                __syncthreads();
+                for (int s = tid; s < ns; s += T) {
+                    const int v = A.velo_idx[s0 + s];
+                    if (v >= 0) atomicMin(&vmin[v], __float_as_uint(A.ghost_prob[s0 + s]));
+                }
+                __syncthreads();
+                for (int s = tid; s < ns; s += T) {
+                    const int v = A.velo_idx[s0 + s];
+                    if (v >= 0 && A.ghost_prob[s0 + s] - __uint_as_float(vmin[v]) >= P.clone_margin)
                         A.velo_idx[s0 + s] = -2 - v;
-                        break;
+                }
+            } else {
+                for (int s = tid; s < ns; s += T) {
+                    const int v = A.velo_idx[s0 + s];
+                    if (v < 0) continue;
+                    const float p = A.ghost_prob[s0 + s];
+                    for (int t = 0; t < ns; ++t) {
+                        if (t == s) continue;
+                        int vt = A.velo_idx[s0 + t];
+                        if (vt <= -2) vt = -2 - vt;
+                        if (vt == v && p - A.ghost_prob[s0 + t] >= P.clone_margin) {
+                            A.velo_idx[s0 + s] = -2 - v;
+                            break;
+                        }
                     }
                 }
             }

@@ -147,6 +147,28 @@ extern "C" void st_config_default(st_config* c) {
     c->final_sel = 0;
     c->ghost_max = 0.8;     // Section 4.4
     c->clone_margin = 0.05;
+    {
+        // UT (Section 4.3); the layer z are not given in the paper
+        const double uz[4] = {2327.5, 2372.5, 2597.5, 2642.5};
+        const int us[4] = {0, 1, -1, 0};
+        for (int l = 0; l < 4; ++l) {
+            c->ut_z[l] = uz[l];
+            c->ut_dxdy[l] = us[l] * t5;
+        }
+        c->ut_gamma[0] = 7.707063e-11;  // Table (mag_params)
+        c->ut_gamma[1] = -7.817364e-3;
+        c->ut_kick = 1200.0;
+        // Table (ut_search_window_values): loose windows of UTaX, UTaU, UTbV;
+        // tight windows of UTaU, UTbV, UTbX
+        const double lw[16] = {0.8333, 3.3333, 1.2, 8.5, 0.8333, 3.3333, 1.2, 8.5,
+                               1.3333, 3.3333, 1.5, 9.5, 0, 0, 0, 0};
+        const double tw[16] = {0, 0, 0, 0, 0.2, 0.6, 0.5, 2.0, 0.4, 1.2, 1.0, 4.0, 0.4, 1.2, 1.0, 4.0};
+        for (int k = 0; k < 16; ++k) {
+            c->ut_loose[k] = lw[k];
+            c->ut_tight[k] = tw[k];
+        }
+        c->ut_min_hits = 3;  // "more than two associated UT hits"
+    }
     c->threads_seed = 256;
     c->threads_build = 512;
     c->threads_match = 256;
@@ -176,8 +198,12 @@ bool derive_params(const st_config& c, DevParams& P, std::string& err) {
         c.hough_clusters > 8 || !(c.hough_ty_max + c.hough_ty_in > 0))
         return fail("Hough parameters: bins in [2, 64], fine and clusters in [1, 8], non-empty t_y range");
     if (c.final_sel < 0 || c.final_sel > 1 || (c.final_sel && c.velo_unique) || !(c.ghost_max > 0) ||
-        !(c.clone_margin >= 0))
-        return fail("final_sel must be 0 or 1 and excludes velo_unique; ghost_max > 0, clone_margin >= 0");
+        !(c.clone_margin > 0))
+        return fail("final_sel must be 0 or 1 and excludes velo_unique; ghost_max and clone_margin > 0");
+    if (c.ut_min_hits < 0 || c.ut_min_hits > 4 || !(c.ut_kick > 0))
+        return fail("ut_min_hits must be in [0, 4] and ut_kick > 0");
+    for (int l = 0; l < 4; ++l)
+        if (!(std::fabs(c.ut_z[l] - c.z_velo) > 0)) return fail("UT layers must not sit at z_velo");
     if (!(c.invp_b != 0.0) || !(c.invp_a * c.invp_a + 4 * c.invp_b / c.p_min >= 0))
         return fail("Eq. invp parameters give no momentum limit");
     if (c.threads_seed < 64 || c.threads_seed > kMaxThreads || c.threads_seed % 32 ||

@@ -42,6 +42,9 @@ class StConfig(C.Structure):
         ("uv_mode", C.c_int32), ("hough_bins", C.c_int32), ("hough_fine", C.c_int32),
         ("hough_clusters", C.c_int32), ("hough_ty_max", C.c_double), ("hough_ty_in", C.c_double),
         ("final_sel", C.c_int32), ("pad3", C.c_int32), ("ghost_max", C.c_double), ("clone_margin", C.c_double),
+        ("ut_z", C.c_double * 4), ("ut_dxdy", C.c_double * 4), ("ut_gamma", C.c_double * 2),
+        ("ut_kick", C.c_double), ("ut_loose", C.c_double * 16), ("ut_tight", C.c_double * 16),
+        ("ut_min_hits", C.c_int32), ("pad4", C.c_int32),
     ]
 
 

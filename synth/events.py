@@ -67,6 +67,16 @@ class Detector:
     y_acc: float = 2500.0
     tx_max: float = 0.3
     ty_max: float = 0.25
+    # UT (four layers x-u-v-x in front of the magnet).  Between the VELO and
+    # the UT a track bends as x(z) = x_V + tx_V dz + gamma dz^2 (dz = z -
+    # z_velo) with gamma = ut_gamma_a + ut_gamma_b * q/p (per MeV), the
+    # parametrisation the reconstruction uses; the SciFi segment is not
+    # affected (the bend is folded into the kink).
+    ut_z: tuple = (2327.5, 2372.5, 2597.5, 2642.5)
+    ut_stereo_sign: tuple = (0, +1, -1, 0)
+    ut_gamma_a: float = 7.707063e-11
+    ut_gamma_b: float = -7.817364e-3
+    ut_x_acc: float = 900.0
 
     @property
     def z_arr(self) -> np.ndarray:
@@ -119,6 +129,13 @@ class EventBatch:
     velo: np.ndarray
     velo_track: np.ndarray
     meta: Dict[str, object] = field(default_factory=dict)
+    # UT hits (CSR per event): measured x at y = 0 along the strip, layer 0..3,
+    # truth track id (-1 noise), and the float64 value before rounding
+    ut_off: Optional[np.ndarray] = None
+    ut_x: Optional[np.ndarray] = None
+    ut_layer: Optional[np.ndarray] = None
+    ut_track: Optional[np.ndarray] = None
+    ut_x_exact: Optional[np.ndarray] = None
 
     @property
     def n_events(self) -> int:
@@ -135,6 +152,10 @@ class EventBatch:
     def exact_hits_of(self, e: int):
         s, t = int(self.ev_off[e]), int(self.ev_off[e + 1])
         return self.x_exact[s:t], self.zone[s:t]
+
+    def ut_of(self, e: int):
+        s, t = int(self.ut_off[e]), int(self.ut_off[e + 1])
+        return self.ut_x[s:t], self.ut_layer[s:t]
 
     def velo_of(self, e: int) -> np.ndarray:
         s, t = int(self.velo_off[e]), int(self.velo_off[e + 1])
@@ -167,8 +188,14 @@ class EventBatch:
         trk["trk_ev"] = np.repeat(np.arange(len(events)), np.diff(trk_off)).astype(np.int32)
         velo_off, (velo, vt), _ = gather(self.velo_off, self.velo, self.velo_track)
         vt = np.where(vt >= 0, remap[vt], -1).astype(np.int32)
+        ut = {}
+        if self.ut_off is not None:
+            ut_off, (ux, ul, ut_t, uxe), _ = gather(self.ut_off, self.ut_x, self.ut_layer, self.ut_track,
+                                                     self.ut_x_exact)
+            ut = dict(ut_off=ut_off, ut_x=ux, ut_layer=ul, ut_track=np.where(ut_t >= 0, remap[ut_t], -1).astype(np.int32),
+                      ut_x_exact=uxe)
         return EventBatch(self.det, ev_off, x, z, dxdy, zone, xe, ht, trk_off, trk,
-                          velo_off, velo, vt, dict(self.meta))
+                          velo_off, velo, vt, dict(self.meta), **ut)
 
 
 # ---------------------------------------------------------------------------
@@ -221,13 +248,16 @@ def make_events(n_events: int, *, seed: int, tracks=("poisson", 150.0),
                 p_range=(2.0, 100.0), noise_frac: float = 0.3, eff: float = 0.98,
                 sigma_x: float = 0.07, velo_ghosts_per_track: float = 0.2,
                 velo_sigma=(0.015, 2.0e-4), det: Detector = DEFAULT_DETECTOR,
-                ntracks: Optional[np.ndarray] = None) -> EventBatch:
+                ntracks: Optional[np.ndarray] = None, ut_sigma: float = 0.05,
+                ut_eff: float = 0.99) -> EventBatch:
     """Generate `n_events` events.
 
     tracks: ("fixed", n) | ("poisson", mean) | ("lognormal", median, sigma, lo, hi)
     noise_frac: noise hits per event = round(noise_frac * signal hits of the event)
     velo_ghosts_per_track: VELO ghosts per event = round(g * tracks of the event)
     velo_sigma: (position mm, slope) Gaussian smearing of true VELO states
+    ut_sigma, ut_eff: UT hit smearing (mm) and layer efficiency; UT noise hits
+        are noise_frac of the event's UT signal hits, uniform in x and layer
     """
     rng = np.random.default_rng(seed)
     nt = _tracks_per_event(rng, n_events, tracks) if ntracks is None else np.asarray(ntracks, np.int64)
@@ -303,10 +333,39 @@ def make_events(n_events: int, *, seed: int, tracks=("poisson", 150.0),
 
     trk_off = np.zeros(n_events + 1, np.int64)
     np.cumsum(nt, out=trk_off[1:])
+
+    # UT hits, from their own random stream (the SciFi and VELO outputs do not
+    # depend on whether UT hits are made)
+    urng = np.random.default_rng([seed, 7])
+    uz = np.asarray(det.ut_z, np.float64)
+    ut_t = np.tan(np.radians(det.stereo_angle_deg)) * np.asarray(det.ut_stereo_sign, np.float64)
+    dz = uz - det.z_velo
+    gam = det.ut_gamma_a + det.ut_gamma_b * tr["q"] / (tr["p"] * 1000.0)
+    UX = tr["txv"][:, None] * uz[None, :] + gam[:, None] * dz[None, :] ** 2
+    UY = tr["ty"][:, None] * uz[None, :]
+    uxm = UX - UY * ut_t[None, :]
+    if ut_sigma > 0:
+        uxm = uxm + urng.normal(0.0, ut_sigma, size=uxm.shape)
+    ukeep = (urng.random(uxm.shape) < ut_eff) & (np.abs(uxm) < det.ut_x_acc)
+    uti, uli = np.nonzero(ukeep)
+    u_ev = np.concatenate([trk_ev[uti], np.repeat(np.arange(n_events), np.rint(noise_frac * np.bincount(
+        trk_ev[uti], minlength=n_events)).astype(np.int64))])
+    n_un = len(u_ev) - len(uti)
+    u_x = np.concatenate([uxm[uti, uli], urng.uniform(-det.ut_x_acc, det.ut_x_acc, n_un)])
+    u_l = np.concatenate([uli, urng.integers(0, 4, n_un)]).astype(np.int32)
+    u_trk = np.concatenate([uti, -np.ones(n_un, np.int64)])
+    uorder = np.lexsort((urng.random(len(u_ev)), u_ev))
+    u_ev, u_x, u_l, u_trk = u_ev[uorder], u_x[uorder], u_l[uorder], u_trk[uorder]
+    ut_off = np.zeros(n_events + 1, np.int64)
+    np.cumsum(np.bincount(u_ev, minlength=n_events), out=ut_off[1:])
+    ut_hit = -np.ones((T, 4), np.int64)
+    usig = u_trk >= 0
+    ut_hit[u_trk[usig], u_l[usig]] = (np.arange(len(u_ev)) - ut_off[u_ev])[usig]
+
     trk = {
         "trk_ev": trk_ev.astype(np.int32), "a": tr["a"], "b": tr["b"], "c": tr["c"],
         "ty": tr["ty"], "y0": np.zeros(T), "p": tr["p"], "q": tr["q"],
-        "tx_velo": tr["txv"], "half": half, "layer_hit": layer_hit,
+        "tx_velo": tr["txv"], "half": half, "layer_hit": layer_hit, "ut_hit": ut_hit,
     }
     zf = z.astype(np.float32)
     return EventBatch(
@@ -317,6 +376,8 @@ def make_events(n_events: int, *, seed: int, tracks=("poisson", 150.0),
         velo_off=velo_off, velo=v_all.astype(np.float32), velo_track=v_trk.astype(np.int32),
         meta={"seed": seed, "tracks": tracks, "noise_frac": noise_frac, "eff": eff,
               "sigma_x": sigma_x, "p_range": p_range},
+        ut_off=ut_off, ut_x=u_x.astype(np.float32), ut_layer=u_l, ut_track=u_trk.astype(np.int32),
+        ut_x_exact=u_x.astype(np.float64),
     )
 
 

@@ -47,6 +47,13 @@ MUTATIONS = {
     "ghost_cut_reversed": ("if (!(p < c->ghost_max)) velo_idx[s] = -1;", "if (p < c->ghost_max) velo_idx[s] = -1;"),
     "clone_margin_sign": ("if (d >= c->clone_margin) drop[s] = 1;", "if (-d >= c->clone_margin) drop[s] = 1;"),
     "nn_hits_feature": ("chi2[s], asinh(1.0 / rho), (double)seed_nhits[s]};", "chi2[s], asinh(1.0 / rho), chi2[s]};"),
+    "ut_refit_sign": ("g = (ut_x[best] + yt * c->ut_dxdy[l] - xV - txV * dz) / (dz * dz);",
+                      "g = (ut_x[best] - yt * c->ut_dxdy[l] - xV - txV * dz) / (dz * dz);"),
+    "ut_window_p": ("w[0] + w[1] * inv_p_gev", "w[0] + w[1] / inv_p_gev"),
+    "ut_no_refit": ("                g = (ut_x[best] + yt * c->ut_dxdy[l] - xV - txV * dz) / (dz * dz);\n", ""),
+    "ut_min_hits": ("if (n < c->ut_min_hits) velo_idx[s] = -1;", "if (n <= c->ut_min_hits) velo_idx[s] = -1;"),
+    "ut_windows_swapped": ("found ? &c->ut_tight[4 * l] : &c->ut_loose[4 * l]",
+                           "found ? &c->ut_loose[4 * l] : &c->ut_tight[4 * l]"),
     "state_slope": ("s->tx_s = cd->th[1] + cd->th[2] * (2.0 * zb + 3.0 * c->d_ratio * zb * zb);",
                     "s->tx_s = cd->th[1];"),
 }

@@ -494,10 +494,87 @@ def check_final_selection(L=None, zmx=None, n_events=6):
     assert nshared > 0 and ndropped > 0
 
 
+# ---------------------------------------------------------------------------
+# UT hits of the Long tracks (Section 4.3)
+# ---------------------------------------------------------------------------
+
+def _ut_case(seed, n_tracks=6):
+    """Noise-free, unsmeared, fully efficient tracks with UT hits; the true
+    seed states at z_state and the true VELO segment of each track."""
+    b = make_events(1, seed=seed, tracks=("fixed", n_tracks), noise_frac=0.0, eff=1.0, sigma_x=0.0,
+                    p_range=(3.5, 100.0), velo_ghosts_per_track=0.0, velo_sigma=(0, 0), ut_sigma=0.0,
+                    ut_eff=1.0)
+    tr = b.tracks_of(0)
+    zs = 7826.0
+    st = np.stack([DET.x_model(tr["a"], tr["b"], tr["c"], zs), tr["ty"] * zs, DET.x_slope(tr["b"], tr["c"], zs),
+                   tr["ty"]], 1)
+    # the true VELO states in float64 (the batch stores them as float32), one per track
+    velo = np.stack([tr["tx_velo"] * DET.z_velo, tr["ty"] * DET.z_velo, tr["tx_velo"], tr["ty"]], 1)
+    vidx = np.arange(len(tr["p"]), dtype=np.int32)
+    ux, ul = b.ut_x_exact[b.ut_off[0]:b.ut_off[1]], b.ut_layer[b.ut_off[0]:b.ut_off[1]]
+    gam_true = DET.ut_gamma_a + DET.ut_gamma_b * tr["q"] / (tr["p"] * 1000.0)
+    return velo, tr, st, vidx, ux.copy(), ul.copy(), gam_true
+
+
+def check_ut_search(L=None):
+    """(1) noise-free tracks get their four UT hits and, once a hit has been
+    attached, gamma_x equals the generating value (also when the first hit is
+    a stereo one); (2) a hit 0.9x / 1.1x the printed window (Table
+    ut_search_window_values, 1/p from the pair) from its prediction is taken
+    / not taken, for the loose window of UTaX and the tight one of UTbX;
+    (3) Long tracks with fewer than three UT hits are dropped."""
+    const = read_golden_constants()
+    cfg = oracle.default_config(_lib=L)
+    for seed in (501, 502):
+        velo, tr, st, vidx, ux, ul, gt = _ut_case(seed)
+        r = oracle.ut_search(cfg, velo, st, vidx, ux, ul, _lib=L)
+        assert np.array_equal(r["ut_hits"], tr["ut_hit"]), (r["ut_hits"], tr["ut_hit"])
+        assert np.all(r["n_ut"] == 4) and np.array_equal(r["velo_idx"], vidx)
+        assert np.allclose(r["gamma"], gt, rtol=1e-9, atol=1e-18)
+        # without the UTaX hits the first hit is on the u layer (stereo)
+        keep = ul != 0
+        remap = -np.ones(len(ux), np.int64)
+        remap[keep] = np.arange(keep.sum())
+        r2 = oracle.ut_search(cfg, velo, st, vidx, ux[keep], ul[keep], _lib=L)
+        want = np.where(tr["ut_hit"] >= 0, remap[np.maximum(tr["ut_hit"], 0)], -1)
+        want[:, 0] = -1
+        assert np.array_equal(r2["ut_hits"], want)
+        assert np.allclose(r2["gamma"], gt, rtol=1e-9, atol=1e-18)
+        # (2) window edges
+        k = 0
+        dz = np.array(cfg.ut_z[:]) - cfg.z_velo
+        xV, yV, txV, tyV = (float(v) for v in velo[vidx[k]])
+        qop = (st[k, 2] - txV) / cfg.ut_kick
+        inv_p = 1000.0 * abs(qop)
+        lo = [const[("ut_loose", 4 * 0 + i)] for i in range(4)]
+        win_l = min(max(lo[0] + lo[1] * inv_p, lo[2]), lo[3])
+        g0 = const[("ut_gamma", 0)] + const[("ut_gamma", 1)] * qop
+        x_pred0 = xV + txV * dz[0] + g0 * dz[0] ** 2
+        ti = [const[("ut_tight", 4 * 3 + i)] for i in range(4)]
+        win_t = min(max(ti[0] + ti[1] * inv_p, ti[2]), ti[3])
+        h0, h3 = tr["ut_hit"][k, 0], tr["ut_hit"][k, 3]
+        for frac, inside in ((0.9, True), (1.1, False)):
+            for sgn in (1.0, -1.0):
+                x = ux.copy()
+                x[h0] = x_pred0 + sgn * frac * win_l
+                r = oracle.ut_search(cfg, velo, st[k:k + 1], vidx[k:k + 1], x, ul, _lib=L)
+                assert (r["ut_hits"][0, 0] == h0) == inside
+                x = ux.copy()
+                x[h3] += sgn * frac * win_t  # the prediction there is exact once UTaX is attached
+                r = oracle.ut_search(cfg, velo, st[k:k + 1], vidx[k:k + 1], x, ul, _lib=L)
+                assert r["ut_hits"][0, 0] == h0 and (r["ut_hits"][0, 3] == h3) == inside
+        # (3) the hit-count requirement: drop two or one of track k's hits
+        for n_drop, kept in ((2, False), (1, True)):
+            keep = np.ones(len(ux), bool)
+            keep[tr["ut_hit"][k, :n_drop]] = False
+            r = oracle.ut_search(cfg, velo, st[k:k + 1], vidx[k:k + 1], ux[keep], ul[keep], _lib=L)
+            assert r["n_ut"][0] == 4 - n_drop and (r["velo_idx"][0] >= 0) == kept
+
+
 ALL_CHECKS = (check_paper_constants, check_window_closed_forms, check_k3_chord,
               check_noise_free_recovery, check_triplets_brute_force, check_clone_kill_pairwise,
               check_tolerance_boundaries, check_matching_grid, check_hough_noise_free,
-              check_hough_clusters, check_final_selection)
+              check_hough_clusters, check_final_selection, check_ut_search)
 
 
 # ---------------------------------------------------------------------------
@@ -587,6 +664,37 @@ def test_uv_recovers_true_stereo_hits(ocfg):
 
 def test_final_selection(zmx_calibrated):
     check_final_selection(zmx=zmx_calibrated)
+
+
+def test_ut_search():
+    check_ut_search()
+
+
+def test_ut_efficiency_on_synthetic_events(zmx_calibrated):
+    """On the Run-3-like sample almost every true Long track keeps at least
+    three UT hits, and the attached hits are mostly the track's own."""
+    b = workload("run3", n_events=20)
+    cfg = oracle.default_config(zmx=zmx_calibrated)
+    res = oracle.seeding_batch(cfg, b)
+    n_true = n_kept = n_hit = n_own = 0
+    for e, r in enumerate(res):
+        s = r["seeds"]
+        st = np.stack([s["x_s"], s["y_s"], s["tx_s"], s["ty_s"]], 1)
+        m = oracle.matching_event(cfg, b.velo_of(e), st)
+        ux, ul = b.ut_of(e)
+        u = oracle.ut_search(cfg, b.velo_of(e), st, m["velo_idx"], ux, ul)
+        vt = b.velo_track[b.velo_off[e]:b.velo_off[e + 1]]
+        utt = b.ut_track[b.ut_off[e]:b.ut_off[e + 1]]
+        for k in np.nonzero(m["velo_idx"] >= 0)[0]:
+            t = vt[m["velo_idx"][k]]
+            if t < 0 or truth_track_of(b, e, s["hits"][k])[0] != t:
+                continue
+            n_true += 1
+            n_kept += u["velo_idx"][k] >= 0
+            hs = u["ut_hits"][k][u["ut_hits"][k] >= 0]
+            n_hit += len(hs)
+            n_own += int(np.sum(utt[hs] == t))
+    assert n_kept / n_true > 0.98 and n_own / n_hit > 0.9, (n_kept / n_true, n_own / n_hit)
 
 
 def test_hough_noise_free():
