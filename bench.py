@@ -364,6 +364,10 @@ def main():
                                                  flush, stream, args.steps, nn=ghost_nn_weights())
         result["final_selection"]["weights"] = "seeded stand-in (the trained weights are not published)"
         log(f"final_selection: {result['final_selection']}")
+        graph.st_graph_launch(stream)  # the default configuration's outputs again
+        stream.synchronize()
+        result["ut"] = time_ut(st, ctx, db, out, flush, stream, args.steps)
+        log(f"ut: {result['ut']}")
 
     if args.quick:
         graph.close()
@@ -506,6 +510,31 @@ def time_variant(st, overrides, db, out, cap, n_ev, flush, stream, steps, nn=Non
     return {"value": n_ev * steps / (tot / 1000.0), "unit": "events/s", "ms_per_step": tot / steps,
             "kernel_ms": kms, "seeds_per_event": seeds / n_ev,
             "config": {k: v for k, v in overrides.items() if k != "zmx"}}
+
+
+def time_ut(st, ctx, db, out, flush, stream, steps):
+    """ut_run (Section 4.3) on the batch's Long tracks after a batched step;
+    the matching result is restored (untimed) before every timed call."""
+    import torch
+    graph_out = out.velo_idx.clone(), out.chi2.clone(), out.n_long.clone()
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for k in range(steps + 3):
+            out.velo_idx.copy_(graph_out[0])
+            out.chi2.copy_(graph_out[1])
+            out.n_long.copy_(graph_out[2])
+            flush.fill_(1)
+            e0.record(stream)
+            ctx.ut_run(db.velo_s, out.seeds, db.ut, out.long, out.ut_out, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 3:
+                tot += e0.elapsed_time(e1)
+    n_long = int((graph_out[0][: int(out.ev_off[-1])] >= 0).sum())
+    kept = int(out.n_long[: db.n_events].sum())
+    return {"ms_per_call": tot / steps, "long_tracks_in": n_long, "long_tracks_kept": kept,
+            "ut_hits_per_event": float(db.ut_x.numel()) / db.n_events}
 
 
 def poll_grow(st, ctx, ticket, n_events, timeout_us=60_000_000):

@@ -247,6 +247,40 @@ int seeding_run(st_ctx* ctx, const st_hits* hits, st_seeds* seeds, void* cuda_st
 int matching_run(st_ctx* ctx, const st_velo* velo, const st_seeds* seeds, st_long* out,
                  void* cuda_stream);
 
+/* UT hits of a batch (CSR), DEVICE memory: x is the measured coordinate at
+ * y = 0 along the strip, layer 0..3 = UTaX, UTaU, UTbV, UTbX. */
+typedef struct {
+    int64_t n_events;
+    const int64_t* ev_off;  /* [n_events + 1] into x / layer */
+    const float* x;
+    const int32_t* layer;
+} st_ut_hits;
+
+/* UT search output, one entry per seed (st_seeds indexing), DEVICE:
+ *   hits  [cap*4] int32: event-local UT hit index per UT layer, -1 = none
+ *   n_hits[cap]   int8:  UT hits attached
+ *   gamma [cap]   float: the final gamma_x of Eq. (velo_ut_extrapolation) */
+typedef struct {
+    int32_t* hits;
+    int8_t* n_hits;
+    float* gamma;
+} st_ut_out;
+
+/* UT hits of the Long tracks (Section 4.3), after matching_run on the same
+ * seeds: for every seed with out->velo_idx >= 0 the VELO segment is
+ * extrapolated with Eq. (velo_ut_extrapolation), gamma_x from Eq.
+ * (gamma_parametrisation) at the pair's q/p = (tx_SciFi - tx_VELO) / ut_kick,
+ * through the UT layers in order: until a hit is found a layer is searched in
+ * its loose window min(max(A_L + B_L/p, x_min), x_max) and the closest hit in
+ * it is attached and refits gamma_x through itself; later layers use their
+ * tight windows (closest hit attached).  Ties go to the smaller x, then the
+ * smaller hit index.  A Long track with fewer than cfg.ut_min_hits UT hits is
+ * dropped (velo_idx = -1, chi2 = 0) and n_long (if given) is recounted.  An
+ * event with a UT layer outside [0, 4) or a non-finite x gets
+ * seeds->status = ST_EINVAL and no UT hits.  Errors as seeding_run. */
+int ut_run(st_ctx* ctx, const st_velo* velo, const st_seeds* seeds, const st_ut_hits* ut, st_long* out,
+           st_ut_out* ut_out, void* cuda_stream);
+
 /* Weights of the ghost network (Section 4.4): ST_GHOST_NN_SIZE floats, HOST
  * memory, copied.  Layout: input mean[8] and inverse scale[8] (each input is
  * standardised as (f - mean) * inv_scale), W1[32][8], b1[32] (hidden layer,

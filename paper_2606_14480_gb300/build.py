@@ -1,6 +1,6 @@
 """Build libst.so (the CUDA library) in-tree with nvcc for sm_103a.
 
-The two translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 paper_2606_14480_gb300/libst.so (CUDA runtime linked statically).
 """
 
@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libst.so")
-SOURCES = ("st_kernels.cu", "st_runtime.cu", "st_static.cu")
+SOURCES = ("st_kernels.cu", "st_runtime.cu", "st_static.cu", "st_ut.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -599,7 +599,9 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     float4* vfit = reinterpret_cast<float4*>(vstore + kUvStore);   // (chi2_y, beta, wm, zm) of the fit
     uint2* vmeta = reinterpret_cast<uint2*>(vfit + kUvStore);      // (seed, pass | initial hit << 1)
     float* g_xs = reinterpret_cast<float*>(vmeta + kUvStore);
-    ull* tloc = reinterpret_cast<ull*>(g_xs + 6 * CC) + tid * kTripLocal;  // this thread's triplet buffer
+    // this thread's triplet buffer: entry q at tloc[q * T] (the block's first
+    // entries are contiguous, so a round touches few cache lines)
+    ull* tloc = reinterpret_cast<ull*>(g_xs + 6 * CC) + tid;
     uint8_t* hcl = reinterpret_cast<uint8_t*>(reinterpret_cast<ull*>(g_xs + 6 * CC) + kTripLocal * kMaxThreads);
     uint8_t* hn = hcl + 8 * CC;  // Hough variant: kept clusters per seed and their count
     __shared__ int s_nvalid;
@@ -713,7 +715,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     for (int q = 0; q < c; ++q) {
                         const ull key = pack_trip(it, k1, k3, lo2 + q);
                         if (direct) trip[wofs + w + q] = key;
-                        else if (w + q < kTripLocal) tloc[w + q] = key;
+                        else if (w + q < kTripLocal) tloc[(w + q) * T] = key;
                     }
                     w += c;
                     ++k3;
@@ -732,7 +734,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 if (again) {
                     walk(true, wofs);
                 } else {
-                    for (int q = 0; q < nt; ++q) trip[wofs + q] = tloc[q];
+                    for (int q = 0; q < nt; ++q) trip[wofs + q] = tloc[q * T];
                 }
             }
             __syncthreads();

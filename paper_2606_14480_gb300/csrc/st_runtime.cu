@@ -21,6 +21,7 @@
 #include "st.h"
 #include "st_host.h"
 #include "st_kernels.cuh"
+#include "st_ut.cuh"
 
 using namespace st;
 
@@ -797,6 +798,55 @@ extern "C" int matching_run(st_ctx* ctx, const st_velo* velo, const st_seeds* se
         return set_err(ctx, ST_EINVAL, "matching_run: null seeds or output array");
     ST_CUDA(ctx, cudaSetDevice(ctx->device));
     return run_matching(ctx, ctx->ws, *velo, *seeds, *out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ut_run(st_ctx* ctx, const st_velo* velo, const st_seeds* seeds, const st_ut_hits* ut, st_long* out,
+                      st_ut_out* uo, void* stream) {
+    if (!ctx) return ST_EINVAL;
+    if (!velo || !seeds || !ut || !out || !uo || !seeds->ev_off || !seeds->state || !seeds->status ||
+        !out->velo_idx || !out->chi2 || !uo->hits || !uo->n_hits || !uo->gamma)
+        return set_err(ctx, ST_EINVAL, "ut_run: null argument or array");
+    if (ut->n_events != velo->n_events || ut->n_events < 0 ||
+        (ut->n_events > 0 && (!ut->ev_off || !ut->x || !ut->layer || !velo->ev_off || !velo->state)))
+        return set_err(ctx, ST_EINVAL, "ut_run: event counts differ or null hit arrays");
+    if (ut->n_events == 0) return ST_OK;
+    ST_CUDA(ctx, cudaSetDevice(ctx->device));
+    const st_config& c = ctx->cfg;
+    UtParams U;
+    U.z_velo = static_cast<float>(c.z_velo);
+    for (int l = 0; l < 4; ++l) {
+        const double dz = c.ut_z[l] - c.z_velo;
+        U.dz[l] = static_cast<float>(dz);
+        U.dz2[l] = static_cast<float>(dz * dz);
+        U.t[l] = static_cast<float>(c.ut_dxdy[l]);
+    }
+    U.gA = static_cast<float>(c.ut_gamma[0]);
+    U.gB = static_cast<float>(c.ut_gamma[1]);
+    U.inv_kick = static_cast<float>(1.0 / c.ut_kick);
+    for (int k = 0; k < 16; ++k) {
+        U.loose[k] = static_cast<float>(c.ut_loose[k]);
+        U.tight[k] = static_cast<float>(c.ut_tight[k]);
+    }
+    U.min_hits = c.ut_min_hits;
+    UtArgs a;
+    a.n_events = ut->n_events;
+    a.ut_off = ut->ev_off;
+    a.ut_x = ut->x;
+    a.ut_layer = ut->layer;
+    a.velo_off = velo->ev_off;
+    a.velo = velo->state;
+    a.seed_off = seeds->ev_off;
+    a.seed_state = seeds->state;
+    a.velo_idx = out->velo_idx;
+    a.chi2 = out->chi2;
+    a.n_long = out->n_long;
+    a.status = seeds->status;
+    a.ut_hits = uo->hits;
+    a.ut_n = uo->n_hits;
+    a.gamma = uo->gamma;
+    const int grid = static_cast<int>(std::min<int64_t>(ut->n_events, int64_t(ctx->n_sms) * 6));
+    ST_CUDA(ctx, launch_ut(U, a, grid, static_cast<cudaStream_t>(stream)));
+    return ST_OK;
 }
 
 extern "C" int st_set_ghost_nn(st_ctx* ctx, const float* weights, int32_t n) {

@@ -66,6 +66,14 @@ class StLong(C.Structure):
     _fields_ = [("velo_idx", _P), ("chi2", _P), ("n_long", _P), ("ghost_prob", _P)]
 
 
+class StUtHits(C.Structure):
+    _fields_ = [("n_events", C.c_int64), ("ev_off", _P), ("x", _P), ("layer", _P)]
+
+
+class StUtOut(C.Structure):
+    _fields_ = [("hits", _P), ("n_hits", _P), ("gamma", _P)]
+
+
 COUNTER_NAMES = ("pairs", "triplets", "ext_ok", "cands", "kept", "uv_init", "uv_cands", "seeds",
                  "match_pairs", "match_presel", "matched", "hits", "events")
 
@@ -106,6 +114,8 @@ SIGNATURES = {
     "st_read_counters": ([_P, C.POINTER(StCounters), C.c_int], C.c_int),
     "st_set_timing": ([_P, C.c_int], C.c_int),
     "st_set_ghost_nn": ([_P, _P, C.c_int32], C.c_int),
+    "ut_run": ([_P, C.POINTER(StVelo), C.POINTER(StSeeds), C.POINTER(StUtHits), C.POINTER(StLong),
+                C.POINTER(StUtOut), _P], C.c_int),
     "st_kernel_ms": ([_P, C.POINTER(C.c_float * 4)], C.c_int),
     "seeding_run_static": ([C.POINTER(StConfig), C.POINTER(StHits), C.POINTER(StSeeds), _P, C.c_char_p,
                             C.c_int32], C.c_int),
@@ -225,6 +235,12 @@ class Context:
         rc = self.lib.matching_run(self.h, C.byref(velo), C.byref(seeds), C.byref(out), _stream_handle(stream))
         return self._check(rc, "matching_run") if check else rc
 
+    def ut_run(self, velo: StVelo, seeds: StSeeds, ut: StUtHits, out: StLong, ut_out: StUtOut, stream=None,
+               check=True):
+        rc = self.lib.ut_run(self.h, C.byref(velo), C.byref(seeds), C.byref(ut), C.byref(out), C.byref(ut_out),
+                             _stream_handle(stream))
+        return self._check(rc, "ut_run") if check else rc
+
     def st_graph_create(self, hits, velo, seeds, out):
         g = _P()
         self._check(self.lib.st_graph_create(self.h, C.byref(hits), C.byref(velo), C.byref(seeds),
@@ -324,9 +340,28 @@ class DeviceBatch:
                            self.max_hits, 0)
         self.velo_s = StVelo(n, _ptr(self.velo_off), _ptr(self.velo))
 
+    def add_ut(self, ut_off, ut_x, ut_layer):
+        """Device copies of the batch's UT hits; sets self.ut (st_ut_hits)."""
+        import torch
+        dev = self.x.device
+
+        def t(a, dt):
+            a = np.ascontiguousarray(a)
+            if a.size == 0:
+                a = np.zeros(1, dtype=a.dtype)
+            return torch.as_tensor(a, dtype=dt).to(dev)
+        self.ut_off = t(ut_off, torch.int64)
+        self.ut_x = t(ut_x, torch.float32)
+        self.ut_layer = t(ut_layer, torch.int32)
+        self.ut = StUtHits(self.n_events, _ptr(self.ut_off), _ptr(self.ut_x), _ptr(self.ut_layer))
+        return self
+
     @classmethod
     def from_synth(cls, batch, device="cuda", **kw):
-        return cls(batch.ev_off, batch.x, batch.zone, batch.velo_off, batch.velo, device=device, **kw)
+        db = cls(batch.ev_off, batch.x, batch.zone, batch.velo_off, batch.velo, device=device, **kw)
+        if getattr(batch, "ut_off", None) is not None:
+            db.add_ut(batch.ut_off, batch.ut_x, batch.ut_layer)
+        return db
 
 
 class DeviceOutputs:
@@ -346,6 +381,10 @@ class DeviceOutputs:
         self.chi2 = torch.zeros(max(cap, 1), dtype=torch.float32, device=dev)
         self.n_long = torch.zeros(max(n_events, 1), dtype=torch.int32, device=dev)
         self.ghost_prob = torch.zeros(max(cap, 1), dtype=torch.float32, device=dev)
+        self.ut_hits = torch.zeros((max(cap, 1), 4), dtype=torch.int32, device=dev)
+        self.ut_n = torch.zeros(max(cap, 1), dtype=torch.int8, device=dev)
+        self.ut_gamma = torch.zeros(max(cap, 1), dtype=torch.float32, device=dev)
+        self.ut_out = StUtOut(_ptr(self.ut_hits), _ptr(self.ut_n), _ptr(self.ut_gamma))
         self.seeds = StSeeds(cap, _ptr(self.ev_off), _ptr(self.hits), _ptr(self.params), _ptr(self.state),
                              _ptr(self.n_hits), _ptr(self.status))
         self.long = StLong(_ptr(self.velo_idx), _ptr(self.chi2), _ptr(self.n_long), _ptr(self.ghost_prob))
@@ -358,7 +397,8 @@ class DeviceOutputs:
                 "status": self.status[: len(ev) - 1].cpu().numpy(),
                 "velo_idx": self.velo_idx[:ns].cpu().numpy(), "chi2": self.chi2[:ns].cpu().numpy(),
                 "n_long": self.n_long[: len(ev) - 1].cpu().numpy(),
-                "ghost_prob": self.ghost_prob[:ns].cpu().numpy()}
+                "ghost_prob": self.ghost_prob[:ns].cpu().numpy(), "ut_hits": self.ut_hits[:ns].cpu().numpy(),
+                "ut_n": self.ut_n[:ns].cpu().numpy(), "ut_gamma": self.ut_gamma[:ns].cpu().numpy()}
 
 
 class HostBuffers:
