@@ -57,6 +57,9 @@ void or_config_default(or_config* c) {
     c->n_iter = 2;
     c->iter_layers[0][0] = 0; c->iter_layers[0][1] = 4; c->iter_layers[0][2] = 11;
     c->iter_layers[1][0] = 3; c->iter_layers[1][1] = 7; c->iter_layers[1][2] = 8;
+    /* a third iteration (HLT2-style use only): T1 and T3 from the first,
+     * the other T2 x-layer */
+    c->iter_layers[2][0] = 0; c->iter_layers[2][1] = 7; c->iter_layers[2][2] = 11;
     c->kappa_c = 1.0e-2;
     c->m_lo = 0.5;
     c->m_hi = 1.5;
@@ -120,10 +123,14 @@ void or_config_default(or_config* c) {
     memcpy(c->ut_loose, lw, sizeof(lw));
     memcpy(c->ut_tight, tw, sizeof(tw));
     c->ut_min_hits = 3;      /* "more than two associated UT hits" */
+    c->iter_mode = 0;
+    for (int it = 0; it < 3; ++it) c->p_min_iter[it] = 0.0;
 }
 
 static int config_ok(const or_config* c) {
-    if (c->n_iter < 1 || c->n_iter > 2) return 0;
+    if (c->n_iter < 1 || c->n_iter > 3 || c->iter_mode < 0 || c->iter_mode > 1) return 0;
+    for (int it = 0; it < 3; ++it)
+        if (c->p_min_iter[it] < 0) return 0;
     for (int it = 0; it < c->n_iter; ++it)
         for (int k = 0; k < 3; ++k)
             if (xslot_of_layer(c->iter_layers[it][k]) < 0) return 0;
@@ -150,6 +157,11 @@ static int config_ok(const or_config* c) {
 /* ------------------------------------------------------------------------ */
 /* track model, Eq. (trackequation): x(z) = a + b zb + c zb^2 (1 + d zb)    */
 /* ------------------------------------------------------------------------ */
+
+/* p_min of an iteration (Section 3.2; HLT2-style runs may set one per iteration) */
+static double pmin_of(const or_config* c, int it) {
+    return it >= 0 && it < 3 && c->p_min_iter[it] > 0 ? c->p_min_iter[it] : c->p_min;
+}
 
 static double fcub(const or_config* c, double z) {
     double zb = z - c->z_ref;
@@ -273,14 +285,14 @@ double or_x0max(const or_config* c) {
 double or_dx3max(const or_config* c, int32_t it) {
     double z1 = c->z[c->iter_layers[it][0]], z3 = c->z[c->iter_layers[it][2]];
     return c->dx3_scale * (z3 - z1) / (2.0 * z1 * c->invp_b) *
-           (-c->invp_a + sqrt(c->invp_a * c->invp_a + 4.0 * c->invp_b / c->p_min));
+           (-c->invp_a + sqrt(c->invp_a * c->invp_a + 4.0 * c->invp_b / pmin_of(c, it)));
 }
 
 /* Eq. alphacorr with k = z1 / (z3 - z1); a z offset (mm) added to z3. */
 double or_alpha_corr(const or_config* c, int32_t it) {
     double z1 = c->z[c->iter_layers[it][0]], z3 = c->z[c->iter_layers[it][2]];
     double k = z1 / (z3 - z1);
-    return c->alpha0 / (k * (c->p_min - c->alpha1));
+    return c->alpha0 / (k * (pmin_of(c, it) - c->alpha1));
 }
 
 /* k3 of Section 3.3.3: deviation of the track model at z2 from the chord
@@ -316,6 +328,7 @@ typedef struct {
     int32_t n_led;
     double tau;
     or_counters cnt;
+    const unsigned char* used; /* hits taken by earlier iterations (HLT2-style mode), or NULL */
 } ev_t;
 
 static void ledger_add(ev_t* E, int kind, int half, double margin, const int32_t* hits, int nh) {
@@ -368,6 +381,7 @@ static int closest_hit(ev_t* E, int zi, double xp, double tol, double scale, int
     for (int k = 0; k < nctx && k < 10; ++k) hh[k] = ctx_hits[k];
     int nh = nctx < 10 ? nctx : 10;
     for (int k = 0; k < E->zn[zi]; ++k) {
+        if (E->used && E->used[E->zl[zi][k].i]) continue;
         double xh = E->zl[zi][k].x;
         double d = fabs(xh - xp);
         double S = dmax2(scale, fabs(xh));
@@ -395,9 +409,9 @@ static int closest_hit(ev_t* E, int zi, double xp, double tol, double scale, int
 /* ------------------------------------------------------------------------ */
 
 static void xz_search(ev_t* E, int half, cvec_t* cv, int32_t* trips, int32_t trips_cap,
-                      int32_t* n_trips) {
+                      int32_t* n_trips, int it0, int it1) {
     const or_config* c = E->c;
-    for (int it = 0; it < c->n_iter; ++it) {
+    for (int it = it0; it < it1; ++it) {
         const int L1 = c->iter_layers[it][0], L2 = c->iter_layers[it][1], L3 = c->iter_layers[it][2];
         const double z1 = c->z[L1], z2 = c->z[L2], z3 = c->z[L3];
         const double alpha = or_alpha_corr(c, it);
@@ -416,6 +430,7 @@ static void xz_search(ev_t* E, int half, cvec_t* cv, int32_t* trips, int32_t tri
         for (int k1 = 0; k1 < E->zn[zi1]; ++k1) {
             const double x1 = E->zl[zi1][k1].x;
             const int32_t h1 = E->zl[zi1][k1].i;
+            if (E->used && E->used[h1]) continue;
             /* two-hit window (Eqs. tolHp, alphacorr and the window limits) */
             const double xc = (z3 + alpha) / z1 * x1;
             const double lo = xc - dx3, hi = xc + dx3;
@@ -423,6 +438,7 @@ static void xz_search(ev_t* E, int half, cvec_t* cv, int32_t* trips, int32_t tri
             for (int k3i = 0; k3i < E->zn[zi3]; ++k3i) {
                 const double x3 = E->zl[zi3][k3i].x;
                 const int32_t h3 = E->zl[zi3][k3i].i;
+                if (E->used && E->used[h3]) continue;
                 {
                     int32_t hh[2] = {h1, h3};
                     double m = fmin(fabs(x3 - lo), fabs(x3 - hi)) / dmax2(S3, fabs(x3));
@@ -448,6 +464,7 @@ static void xz_search(ev_t* E, int half, cvec_t* cv, int32_t* trips, int32_t tri
                 for (int k2 = 0; k2 < E->zn[zi2]; ++k2) {
                     const double x2 = E->zl[zi2][k2].x;
                     const int32_t h2 = E->zl[zi2][k2].i;
+                    if (E->used && E->used[h2]) continue;
                     {
                         int32_t hh[3] = {h1, h3, h2};
                         double m = fmin(fabs(x2 - lo2), fabs(x2 - hi2)) / dmax2(S2, fabs(x2));
@@ -619,6 +636,7 @@ static int uv_seed(ev_t* E, int half, const cand_t* cd, uvc_t* best_out) {
         for (int k = 0; k < E->zn[zi]; ++k) {
             const double xh = E->zl[zi][k].x;
             const int32_t h = E->zl[zi][k].i;
+            if (E->used && E->used[h]) continue;
             /* the stereo hit's y (Section 3.4) */
             const double y = (XI - xh) / tI;
             {
@@ -740,6 +758,7 @@ static int uv_seed_hough(ev_t* E, int half, const cand_t* cd, uvc_t* best_out) {
         const double XL = xmodel(c, cd->th, zL);
         const double SL = xscale(c, cd->th, zL);
         for (int k = 0; k < E->zn[zi]; ++k) {
+            if (E->used && E->used[E->zl[zi][k].i]) continue;
             const double xh = E->zl[zi][k].x;
             ctx[nctx] = E->zl[zi][k].i;
             const double y = (XL - xh) / tL;
@@ -867,50 +886,75 @@ int32_t or_seeding_event(const or_config* c, int32_t n_hits, const double* x,
     }
     for (int z = 0; z < NZONE; ++z) qsort(E.zl[z], (size_t)E.zn[z], sizeof(xi_t), cmp_xi);
 
-    for (int half = 0; half < 2; ++half) {
-        cvec_t cv = {0};
-        xz_search(&E, half, &cv, trips, trips_cap, &nt);
-        clone_kill(&E, half, &cv, n_hits);
-        for (int k = 0; k < cv.n; ++k) {
-            const cand_t* cd = &cv.v[k];
-            if (cands && nc < cands_cap) {
-                or_cand* o = &cands[nc];
-                memcpy(o->hits, cd->hits, sizeof(o->hits));
-                o->half = half; o->iter = cd->iter; o->nx = cd->nx; o->keep = cd->keep;
-                o->h1 = cd->h1; o->h2 = cd->h2; o->h3 = cd->h3; o->id = cd->id;
-                o->a = cd->th[0]; o->b = cd->th[1]; o->c = cd->th[2];
-                o->chi2 = cd->chi2; o->score = cd->score;
-            }
-            nc++;
-            if (!cd->keep) continue;
-            uvc_t u;
-            if (!(c->uv_mode == 1 ? uv_seed_hough(&E, half, cd, &u) : uv_seed(&E, half, cd, &u))) continue;
-            E.cnt.seeds++;
-            if (seeds && ns < seeds_cap) {
-                or_seed* s = &seeds[ns];
-                for (int l = 0; l < OR_NLAYER; ++l) s->hits[l] = -1;
-                for (int q = 0; q < 6; ++q) {
-                    s->hits[X_LAYERS[q]] = cd->hits[q];
-                    s->hits[UV_LAYERS[q]] = u.hits[q];
-                }
-                s->half = half;
-                s->nx = cd->nx;
-                s->nuv = u.n;
-                s->cand_id = cd->id;
-                s->a = cd->th[0]; s->b = cd->th[1]; s->c = cd->th[2];
-                s->chi2x = cd->chi2;
-                s->y0 = u.y0; s->ty = u.ty; s->chi2y = u.chi2;
-                /* state for matching (reading of Section 4.1's z_ref for SciFi) */
-                const double zS = c->z_state, zb = zS - c->z_ref;
-                s->x_s = xmodel(c, cd->th, zS);
-                s->tx_s = cd->th[1] + cd->th[2] * (2.0 * zb + 3.0 * c->d_ratio * zb * zb);
-                s->y_s = u.y0 + u.ty * zS;
-                s->ty_s = u.ty;
-            }
-            ns++;
-        }
-        free(cv.v);
+    /* HLT1: both iterations, one clone kill, UV (Sections 3.2-3.4).  HLT2-style
+     * (iter_mode 1): one iteration at a time, each with its own clone kill and
+     * UV step; the hits of its seeds are removed before the next iteration. */
+    unsigned char* used = NULL;
+    if (c->iter_mode == 1) {
+        used = (unsigned char*)calloc((size_t)(n_hits > 0 ? n_hits : 1), 1);
+        E.used = used;
     }
+    const int n_pass = c->iter_mode == 1 ? c->n_iter : 1;
+    for (int half = 0; half < 2; ++half) {
+        for (int pass = 0; pass < n_pass; ++pass) {
+            cvec_t cv = {0};
+            const int it0 = c->iter_mode == 1 ? pass : 0, it1 = c->iter_mode == 1 ? pass + 1 : c->n_iter;
+            xz_search(&E, half, &cv, trips, trips_cap, &nt, it0, it1);
+            clone_kill(&E, half, &cv, n_hits);
+            int32_t* taken = (int32_t*)malloc(sizeof(int32_t) * 12 * (size_t)(cv.n > 0 ? cv.n : 1));
+            int n_taken = 0;
+            for (int k = 0; k < cv.n; ++k) {
+                const cand_t* cd = &cv.v[k];
+                if (cands && nc < cands_cap) {
+                    or_cand* o = &cands[nc];
+                    memcpy(o->hits, cd->hits, sizeof(o->hits));
+                    o->half = half; o->iter = cd->iter; o->nx = cd->nx; o->keep = cd->keep;
+                    o->h1 = cd->h1; o->h2 = cd->h2; o->h3 = cd->h3; o->id = cd->id;
+                    o->a = cd->th[0]; o->b = cd->th[1]; o->c = cd->th[2];
+                    o->chi2 = cd->chi2; o->score = cd->score;
+                }
+                nc++;
+                if (!cd->keep) continue;
+                uvc_t u;
+                if (!(c->uv_mode == 1 ? uv_seed_hough(&E, half, cd, &u) : uv_seed(&E, half, cd, &u))) continue;
+                E.cnt.seeds++;
+                for (int q = 0; q < 6; ++q) {
+                    if (cd->hits[q] >= 0) taken[n_taken++] = cd->hits[q];
+                    if (u.hits[q] >= 0) taken[n_taken++] = u.hits[q];
+                }
+                if (seeds && ns < seeds_cap) {
+                    or_seed* s = &seeds[ns];
+                    for (int l = 0; l < OR_NLAYER; ++l) s->hits[l] = -1;
+                    for (int q = 0; q < 6; ++q) {
+                        s->hits[X_LAYERS[q]] = cd->hits[q];
+                        s->hits[UV_LAYERS[q]] = u.hits[q];
+                    }
+                    s->half = half;
+                    s->nx = cd->nx;
+                    s->nuv = u.n;
+                    s->cand_id = cd->id;
+                    s->pass = pass;
+                    s->pad = 0;
+                    s->a = cd->th[0]; s->b = cd->th[1]; s->c = cd->th[2];
+                    s->chi2x = cd->chi2;
+                    s->y0 = u.y0; s->ty = u.ty; s->chi2y = u.chi2;
+                    /* state for matching (reading of Section 4.1's z_ref for SciFi) */
+                    const double zS = c->z_state, zb = zS - c->z_ref;
+                    s->x_s = xmodel(c, cd->th, zS);
+                    s->tx_s = cd->th[1] + cd->th[2] * (2.0 * zb + 3.0 * c->d_ratio * zb * zb);
+                    s->y_s = u.y0 + u.ty * zS;
+                    s->ty_s = u.ty;
+                }
+                ns++;
+            }
+            /* hit cleanup: the next iteration does not see this one's seeds' hits */
+            if (used)
+                for (int k = 0; k < n_taken; ++k) used[taken[k]] = 1;
+            free(taken);
+            free(cv.v);
+        }
+    }
+    free(used);
     for (int z = 0; z < NZONE; ++z) free(E.zl[z]);
     if (n_seeds) *n_seeds = ns;
     if (n_cands) *n_cands = nc;

@@ -35,9 +35,8 @@ typedef struct {
     double p_min;                 /* MeV/c */
     double alpha0, alpha1;        /* Eq. alphacorr (MeV/c) */
     double dx3_scale;             /* multiplies Delta x3^max (1 = paper) */
-    int32_t n_iter;               /* 2 in HLT1 */
-    int32_t iter_layers[2][3];    /* (T1, T2, T3) initial x-layers per iteration */
-    int32_t pad0;
+    int32_t n_iter;               /* 2 in HLT1 (up to 3) */
+    int32_t iter_layers[3][3];    /* (T1, T2, T3) initial x-layers per iteration */
     double kappa_c;               /* -s*c_x = kappa_c / p (mm^-1 MeV) */
     double m_lo, m_hi;            /* third-hit band multipliers */
     double c_nsigma;              /* band half-width in units of the c_x resolution */
@@ -88,12 +87,17 @@ typedef struct {
     double ut_loose[16];          /* per layer A_L, B_L (mm GeV), x_min, x_max; zeros: no loose search */
     double ut_tight[16];          /* per layer A_T, B_T, x_min, x_max; zeros: no tight search */
     int32_t ut_min_hits;          /* keep Long tracks with at least this many UT hits (0: keep all) */
-    int32_t pad4;
+    /* HLT2-style iterations (Section 3.1): 0 = independent iterations with one
+     * clone kill at the end (HLT1); 1 = iterations in sequence, each with its
+     * own clone kill and UV step, hits of its seeds removed before the next */
+    int32_t iter_mode;
+    double p_min_iter[3];         /* per-iteration p_min (MeV/c); 0: use p_min */
 } or_config;
 
 typedef struct {
     int32_t hits[OR_NLAYER];      /* event-local hit index per layer, -1 = none */
     int32_t half, nx, nuv, cand_id;
+    int32_t pass, pad;            /* iteration that found it in the HLT2-style mode (else 0) */
     double a, b, c, chi2x;        /* x-z parameters (Eq. trackequation) and chi2 */
     double y0, ty, chi2y;         /* y(z) = y0 + ty z */
     double x_s, y_s, tx_s, ty_s;  /* state at z_state */

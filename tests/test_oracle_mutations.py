@@ -54,6 +54,11 @@ MUTATIONS = {
     "ut_min_hits": ("if (n < c->ut_min_hits) velo_idx[s] = -1;", "if (n <= c->ut_min_hits) velo_idx[s] = -1;"),
     "ut_windows_swapped": ("found ? &c->ut_tight[4 * l] : &c->ut_loose[4 * l]",
                            "found ? &c->ut_loose[4 * l] : &c->ut_tight[4 * l]"),
+    "cleanup_missing": ("for (int k = 0; k < n_taken; ++k) used[taken[k]] = 1;",
+                        "for (int k = 0; k < n_taken; ++k) (void)taken[k];"),
+    "pmin_iter_ignored": ("return it >= 0 && it < 3 && c->p_min_iter[it] > 0 ? c->p_min_iter[it] : c->p_min;",
+                          "return c->p_min;"),
+    "used_t3_ignored": ("                if (E->used && E->used[h3]) continue;\n", ""),
     "state_slope": ("s->tx_s = cd->th[1] + cd->th[2] * (2.0 * zb + 3.0 * c->d_ratio * zb * zb);",
                     "s->tx_s = cd->th[1];"),
 }

@@ -571,10 +571,57 @@ def check_ut_search(L=None):
             assert r["n_ut"][0] == 4 - n_drop and (r["velo_idx"][0] >= 0) == kept
 
 
+# ---------------------------------------------------------------------------
+# HLT2-style iterations in sequence with hit cleanup (Section 3.1)
+# ---------------------------------------------------------------------------
+
+SEQ3 = dict(iter_mode=1, n_iter=3, p_min_iter=[5000.0, 3000.0, 1500.0])
+
+
+def check_sequential_iterations(L=None):
+    """(1) noise-free tracks are found once each with their exact hits, for
+    two and three iterations in sequence; (2) on Run-3-like events no hit of
+    a seed is used by a seed of a later iteration (the cleanup) and every
+    pass finds something; (3) one iteration in sequence equals one HLT1
+    iteration; (4) each iteration's two-hit window is Eq. tolHp at its own
+    p_min (numpy's root of b x0^2 + a x0 = 1/p_min)."""
+    for ov in (dict(iter_mode=1), SEQ3):
+        check_noise_free_recovery(L, None, n_events=3, **ov)
+    cfg = oracle.default_config(_lib=L, **SEQ3)
+    b = workload("run3", n_events=6)
+    res = oracle.seeding_batch(cfg, b, _lib=L)
+    per_pass = np.zeros(3, int)
+    for r in res:
+        s = r["seeds"]
+        for half in (0, 1):
+            taken = set()
+            for p in range(3):
+                sel = s[(s["half"] == half) & (s["pass"] == p)]
+                per_pass[p] += len(sel)
+                hs = {int(h) for h in sel["hits"].ravel() if h >= 0}
+                assert not (hs & taken), (half, p)
+                taken |= hs
+    assert (per_pass > 0).all(), per_pass
+    one_seq = oracle.default_config(_lib=L, iter_mode=1, n_iter=1)
+    one = oracle.default_config(_lib=L, n_iter=1)
+    for e in range(3):
+        x, z = b.hits_of(e)
+        a = oracle.seeding_event(one_seq, x, z, _lib=L)["seeds"]
+        c = oracle.seeding_event(one, x, z, _lib=L)["seeds"]
+        assert sorted(map(tuple, a["hits"])) == sorted(map(tuple, c["hits"]))
+    const = read_golden_constants()
+    aa, bb = const[("invp_a", None)], const[("invp_b", None)]
+    for it, pm in enumerate(SEQ3["p_min_iter"]):
+        roots = np.roots([bb, aa, -1.0 / pm])
+        x0 = min(r.real for r in roots if r.real > 0)
+        z1, z3 = cfg.z[cfg.iter_layers[it][0]], cfg.z[cfg.iter_layers[it][2]]
+        assert oracle.dx3max(cfg, it, _lib=L) == pytest.approx((z3 - z1) / z1 * x0, rel=1e-12)
+
+
 ALL_CHECKS = (check_paper_constants, check_window_closed_forms, check_k3_chord,
               check_noise_free_recovery, check_triplets_brute_force, check_clone_kill_pairwise,
               check_tolerance_boundaries, check_matching_grid, check_hough_noise_free,
-              check_hough_clusters, check_final_selection, check_ut_search)
+              check_hough_clusters, check_final_selection, check_ut_search, check_sequential_iterations)
 
 
 # ---------------------------------------------------------------------------
@@ -664,6 +711,39 @@ def test_uv_recovers_true_stereo_hits(ocfg):
 
 def test_final_selection(zmx_calibrated):
     check_final_selection(zmx=zmx_calibrated)
+
+
+def test_sequential_iterations():
+    check_sequential_iterations()
+
+
+def test_sequential_iterations_reach_lower_momentum():
+    """Section 3.1: later iterations with wider windows find lower-momentum
+    tracks in a cleaned-up event.  Three iterations in sequence (p_min 5, 3,
+    1.5 GeV/c) find more tracks between 2 and 3 GeV/c than HLT1's two, keep
+    the efficiency above 3 GeV/c within 0.5%, and form fewer pairs."""
+    b = workload("run3", n_events=30)
+    out = {}
+    for name, ov in (("hlt1", {}), ("seq3", SEQ3)):
+        res = oracle.seeding_batch(oracle.default_config(**ov), b)
+        eff = {}
+        for lo, hi in ((2.0, 3.0), (3.0, 1e9)):
+            nt = nf = 0
+            for e, r in enumerate(res):
+                tr = b.tracks_of(e)
+                seen = set()
+                for s in r["seeds"]:
+                    t, pur = truth_track_of(b, e, s["hits"])
+                    if t >= 0 and pur >= 0.7:
+                        seen.add(t)
+                good = (tr["p"] > lo) & (tr["p"] <= hi) & ((tr["layer_hit"] >= 0).sum(1) >= 10)
+                nt += good.sum()
+                nf += sum((b.trk_off[e] + k) in seen for k in np.nonzero(good)[0])
+            eff[lo] = nf / nt
+        out[name] = (eff, sum(r["counters"]["pairs"] for r in res))
+    assert out["seq3"][0][2.0] > out["hlt1"][0][2.0] + 0.05, out
+    assert out["seq3"][0][3.0] > out["hlt1"][0][3.0] - 0.005, out
+    assert out["seq3"][1] < out["hlt1"][1], out
 
 
 def test_ut_search():
