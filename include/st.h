@@ -60,9 +60,8 @@ typedef struct {
     double p_min;              /* MeV/c, both iterations (Section 3.2) */
     double alpha0, alpha1;     /* Eq. (alphacorr), MeV/c */
     double dx3_scale;          /* scales Delta x3^max of Eq. (tolHp); 1 = paper */
-    int32_t n_iter;            /* XZ iterations (2 in HLT1) */
-    int32_t iter_layers[2][3]; /* initial x-layers (T1, T2, T3) of each iteration */
-    int32_t pad0;
+    int32_t n_iter;            /* XZ iterations (2 in HLT1, up to 3) */
+    int32_t iter_layers[3][3]; /* initial x-layers (T1, T2, T3) of each iteration */
     double kappa_c;            /* third-hit band centre: -sign(x0)*c_x = kappa_c * (1/p) */
     double m_lo, m_hi;         /* band edges as multiples of the centre */
     double c_nsigma;           /* band widening, in units of the c_x resolution */
@@ -121,7 +120,12 @@ typedef struct {
     double ut_loose[16];       /* per UT layer: A_L (mm), B_L (mm GeV/c), x_min, x_max; zeros = none */
     double ut_tight[16];       /* per UT layer: A_T, B_T, x_min, x_max; zeros = none */
     int32_t ut_min_hits;       /* Long tracks need this many UT hits in ut_run (0 = no requirement) */
-    int32_t pad4;
+    /* Iteration scheme (Section 3.1): 0 = HLT1, independent iterations and one
+     * clone kill at the end; 1 = HLT2-style, iterations in sequence, each with
+     * its own clone kill and UV step, the hits of its seeds removed before
+     * the next iteration */
+    int32_t iter_mode;
+    double p_min_iter[3];      /* per-iteration p_min (MeV/c); 0 = p_min */
 } st_config;
 
 /* Hits of a batch of events (CSR).  All arrays are DEVICE memory.

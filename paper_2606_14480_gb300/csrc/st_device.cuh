@@ -44,8 +44,9 @@ struct DevParams {
     float uz[6], uzb[6], uf_hi[6], uf_lo[6], ut[6], uzt[6];
     float uinv_t[6], uinv_z[6];  // 1/dxdy and 1/z of the stereo slots
     float zc_uv;           // centring z of the y-z line fit (uzt = uz - zc_uv)
-    IterP it[2];
+    IterP it[3];
     int n_iter;
+    int iter_mode;  // 1: iterations in sequence with hit cleanup
     float invp_a, invp_b;
     float ext_tol, chi2x_max, inv_sx2, w_chi2, w5;
     float G[kMasks][3][6]; // least-squares gain per x-hit pattern

@@ -99,8 +99,9 @@ extern "C" void st_config_default(st_config* c) {
     c->alpha1 = -1073.0;
     c->dx3_scale = 1.0;
     c->n_iter = 2;
-    const int il[2][3] = {{0, 4, 11}, {3, 7, 8}};
-    for (int i = 0; i < 2; ++i)
+    // the third row is only used by HLT2-style runs with three iterations
+    const int il[3][3] = {{0, 4, 11}, {3, 7, 8}, {0, 7, 11}};
+    for (int i = 0; i < 3; ++i)
         for (int k = 0; k < 3; ++k) c->iter_layers[i][k] = il[i][k];
     c->kappa_c = 1.0e-2;
     c->m_lo = 0.5;
@@ -170,6 +171,8 @@ extern "C" void st_config_default(st_config* c) {
         }
         c->ut_min_hits = 3;  // "more than two associated UT hits"
     }
+    c->iter_mode = 0;
+    for (int it = 0; it < 3; ++it) c->p_min_iter[it] = 0.0;
     c->threads_seed = 256;
     c->threads_build = 512;
     c->threads_match = 256;
@@ -190,7 +193,10 @@ bool derive_params(const st_config& c, DevParams& P, std::string& err) {
         if (c.dxdy[kXL[k]] != 0.0) return fail("x-layers must have dxdy = 0");
         if (!(std::fabs(c.dxdy[kUL[k]]) > 0.0)) return fail("stereo layers need dxdy != 0");
     }
-    if (c.n_iter < 1 || c.n_iter > 2) return fail("n_iter must be 1 or 2");
+    if (c.n_iter < 1 || c.n_iter > 3) return fail("n_iter must be 1, 2 or 3");
+    if (c.iter_mode < 0 || c.iter_mode > 1) return fail("iter_mode must be 0 or 1");
+    for (int it = 0; it < 3; ++it)
+        if (c.p_min_iter[it] < 0) return fail("p_min_iter must be >= 0");
     if (!(c.p_min > 0) || !(c.sigma_x > 0) || !(c.sigma_y > 0) || !(c.ext_tol > 0) || !(c.uv_tol > 0))
         return fail("p_min, sigma_x, sigma_y, ext_tol and uv_tol must be positive");
     if (c.n_uv_min < 2 || c.n_uv_min > 6) return fail("n_uv_min must be in [2, 6]");
@@ -238,7 +244,11 @@ bool derive_params(const st_config& c, DevParams& P, std::string& err) {
         P.uinv_z[u] = static_cast<float>(1.0 / z);
     }
     P.n_iter = c.n_iter;
+    P.iter_mode = c.iter_mode;
     for (int it = 0; it < c.n_iter; ++it) {
+        const double pmin = c.p_min_iter[it] > 0 ? c.p_min_iter[it] : c.p_min;
+        if (!(c.invp_a * c.invp_a + 4 * c.invp_b / pmin >= 0))
+            return fail("Eq. invp parameters give no momentum limit for an iteration's p_min");
         const int L1 = c.iter_layers[it][0], L2 = c.iter_layers[it][1], L3 = c.iter_layers[it][2];
         IterP& I = P.it[it];
         I.s1 = xslot(L1);
@@ -252,10 +262,10 @@ bool derive_params(const st_config& c, DevParams& P, std::string& err) {
         const double z1 = c.z[L1], z2 = c.z[L2], z3 = c.z[L3];
         // two-hit window: Eqs. (tolHp) and (alphacorr)
         const double k = z1 / (z3 - z1);
-        const double alpha = c.alpha0 / (k * (c.p_min - c.alpha1));
+        const double alpha = c.alpha0 / (k * (pmin - c.alpha1));
         I.scale3 = static_cast<float>((z3 + alpha) / z1);
         I.dx3 = static_cast<float>(c.dx3_scale * (z3 - z1) / (2.0 * z1 * c.invp_b) *
-                                   (-c.invp_a + std::sqrt(c.invp_a * c.invp_a + 4.0 * c.invp_b / c.p_min)));
+                                   (-c.invp_a + std::sqrt(c.invp_a * c.invp_a + 4.0 * c.invp_b / pmin)));
         I.inv_dz31 = static_cast<float>(1.0 / (z3 - z1));
         I.dz21 = static_cast<float>(z2 - z1);
         I.z1 = static_cast<float>(z1);

@@ -25,8 +25,8 @@ class StConfig(C.Structure):
         ("z", C.c_double * 12), ("dxdy", C.c_double * 12), ("z_ref", C.c_double),
         ("d_ratio", C.c_double), ("invp_a", C.c_double), ("invp_b", C.c_double),
         ("p_min", C.c_double), ("alpha0", C.c_double), ("alpha1", C.c_double),
-        ("dx3_scale", C.c_double), ("n_iter", C.c_int32), ("iter_layers", (C.c_int32 * 3) * 2),
-        ("pad0", C.c_int32), ("kappa_c", C.c_double), ("m_lo", C.c_double), ("m_hi", C.c_double),
+        ("dx3_scale", C.c_double), ("n_iter", C.c_int32), ("iter_layers", (C.c_int32 * 3) * 3),
+        ("kappa_c", C.c_double), ("m_lo", C.c_double), ("m_hi", C.c_double),
         ("c_nsigma", C.c_double), ("sigma_x", C.c_double), ("ext_tol", C.c_double),
         ("chi2x_max", C.c_double), ("score_w_chi2", C.c_double), ("score_w5", C.c_double),
         ("uv_init", C.c_int32 * 2), ("n_uv_min", C.c_int32), ("pad1", C.c_int32),
@@ -44,7 +44,7 @@ class StConfig(C.Structure):
         ("final_sel", C.c_int32), ("pad3", C.c_int32), ("ghost_max", C.c_double), ("clone_margin", C.c_double),
         ("ut_z", C.c_double * 4), ("ut_dxdy", C.c_double * 4), ("ut_gamma", C.c_double * 2),
         ("ut_kick", C.c_double), ("ut_loose", C.c_double * 16), ("ut_tight", C.c_double * 16),
-        ("ut_min_hits", C.c_int32), ("pad4", C.c_int32),
+        ("ut_min_hits", C.c_int32), ("iter_mode", C.c_int32), ("p_min_iter", C.c_double * 3),
     ]
 
 

@@ -63,8 +63,10 @@ def test_invalid_config_rejected_without_gpu():
     import ctypes as C
     from paper_2606_14480_gb300 import st
     L = st.library()
-    for bad in (dict(n_uv_min=1), dict(n_iter=3), dict(threads_seed=100), dict(sigma_x=0.0),
-                dict(iter_layers=[[0, 1, 11], [3, 7, 8]])):
+    for bad in (dict(n_uv_min=1), dict(n_iter=4), dict(threads_seed=100), dict(sigma_x=0.0),
+                dict(iter_layers=[[0, 1, 11], [3, 7, 8], [0, 7, 11]]), dict(iter_mode=2),
+                dict(p_min_iter=[0.0, -1.0, 0.0]), dict(uv_mode=2), dict(final_sel=1, velo_unique=1),
+                dict(hough_bins=65), dict(ut_min_hits=5)):
         cfg = st.st_config_default(**bad)
         h = C.c_void_p()
         assert L.st_create(C.byref(cfg), 0, C.byref(h)) == st.ST_EINVAL, bad
