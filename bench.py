@@ -9,18 +9,22 @@ flushed (256 MB write) between timed steps, outside the timed interval.
 
 Reported beside the batched number (one JSON line on stdout):
   e2e           the same batch through pipeline_submit / pipeline_poll with
-                host buffers (copies in the timed region), one batch at a time
+                host buffers (copies in the timed region), two batches in flight
   per_event     the plain per-event launch: seeding_run + matching_run per
                 event on one stream
   served        continuous batching of a Poisson request stream (batch sizes
                 log-uniform 1-4096, log-normal occupancy): events/s, p50/p99
+  uv_hough, final_selection, iterations_hlt2, ut
+                the widened method variants on the same batch (Hough-cluster
+                UV, ghost network + clone removal, HLT2-style iterations,
+                UT hits of the Long tracks)
   roofline      the seeding kernel's FP32 work (units counted by the kernels,
-                per-unit costs fixed in the design doc) per CUDA-event-timed launch
+                per-unit costs in OPS_PER_UNIT) per CUDA-event-timed launch
                 against the FP32 peak; its HBM traffic from the ncu summary
   cpu_baseline  the FP64 oracle on the host cores, bounded sample
 
-`--impl reference` times the oracle (the reference implementation of this
-build) on the same workload instead.  Under torchrun each rank runs its own
+`--impl reference` times the FP64 oracle (the method's reference
+implementation, on the host cores) on the same workload instead.  Under torchrun each rank runs its own
 replica batch; the max step time over ranks is used (no data exchange).
 """
 
@@ -364,6 +368,10 @@ def main():
                                                  flush, stream, args.steps, nn=ghost_nn_weights())
         result["final_selection"]["weights"] = "seeded stand-in (the trained weights are not published)"
         log(f"final_selection: {result['final_selection']}")
+        result["iterations_hlt2"] = time_variant(
+            st, dict(zmx=zmx, iter_mode=1, n_iter=3, p_min_iter=[5000.0, 3000.0, 1500.0], **tuned), db, out, cap,
+            n_ev, flush, stream, args.steps)
+        log(f"iterations_hlt2: {result['iterations_hlt2']}")
         graph.st_graph_launch(stream)  # the default configuration's outputs again
         stream.synchronize()
         result["ut"] = time_ut(st, ctx, db, out, flush, stream, args.steps)

@@ -140,8 +140,8 @@ def lib(path: Optional[str] = None):
 
 
 def default_config(_lib=None, **overrides) -> OrConfig:
-    """The oracle's own defaults (the paper's constants and this build's
-    readings), with keyword overrides (arrays accepted for array fields)."""
+    """The oracle's own defaults (the paper's constants and the readings of
+    its gaps), with keyword overrides (arrays accepted for array fields)."""
     cfg = OrConfig()
     (_lib or lib()).or_config_default(C.byref(cfg))
     apply(cfg, overrides)

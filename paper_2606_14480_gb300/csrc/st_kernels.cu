@@ -202,6 +202,12 @@ __device__ __forceinline__ int zhi(const float* x, const uint16_t* lut, int n, f
     return i;
 }
 
+// hits taken by earlier iterations (HLT2-style mode), one bit per half-local
+// hit position; null when every hit is free
+__device__ __forceinline__ bool is_used(const uint32_t* used, int p) {
+    return used && ((used[p >> 5] >> (p & 31)) & 1u);
+}
+
 struct Trip {
     int pos[6];
     float th[3], dth[3];
@@ -216,8 +222,8 @@ struct Trip {
 // correction dth = G y and the chi2 are then computed from small numbers.
 // Returns 0 (fewer than 5 hits), 1 (chi2 cut) or 2 (candidate).
 __device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, const int* szl,
-                          const uint16_t* lut, const float* sG, const int* sMask, int k1, int k2, int k3,
-                          Trip& o) {
+                          const uint16_t* lut, const float* sG, const int* sMask, const uint32_t* used, int k1,
+                          int k2, int k3, Trip& o) {
     const int p1 = szl[I.s1] + k1, p2 = szl[I.s2] + k2, p3 = szl[I.s3] + k3;
     const float x1 = X[p1], x2 = X[p2], x3 = X[p3];
     const float t13 = (x3 - x1) * I.inv_dz31;
@@ -245,6 +251,7 @@ __device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, co
             for (; k < n; ++k) {
                 const float xh = xs[k];
                 if (xh > xp + P.ext_tol) break;
+                if (is_used(used, st + k)) continue;
                 const float d = fabsf(xh - xp);
                 if (d <= P.ext_tol && (p < 0 || d < bd)) {
                     p = st + k;
@@ -314,7 +321,7 @@ struct UV {
 // with ty averaging.  Xs[u] is the seed's x at stereo slot u.  A chain that
 // can no longer reach n_uv_min stops early (it cannot be selected).
 __device__ void uv_chain(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
-                         const float* Xs, int pass, int kinit, UV& o) {
+                         const uint32_t* used, const float* Xs, int pass, int kinit, UV& o) {
     const int ui = P.uv_init[pass];
     const int pi = szl[6 + ui] + kinit;
     const float yi = (Xs[ui] - X[pi]) * P.uinv_t[ui];
@@ -338,6 +345,7 @@ __device__ void uv_chain(const DevParams& P, const float* X, const int* szl, con
         for (; k < nn; ++k) {
             const float xh = xs[k];
             if (xh > xp + P.uv_tol) break;
+            if (is_used(used, st + k)) continue;
             const float d = fabsf(xh - xp);
             if (d <= P.uv_tol && (best < 0 || d < bd)) {
                 best = st + k;
@@ -368,7 +376,7 @@ __device__ void uv_chain(const DevParams& P, const float* X, const int* szl, con
 // clusters (most populated first, at least n_uv_min, ties to the smaller b)
 // go to out[]; returns how many.
 __device__ int hough_select(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
-                            const float* Xs, int h, uint8_t* out) {
+                            const uint32_t* used, const float* Xs, int h, uint8_t* out) {
     ull s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
@@ -379,6 +387,7 @@ __device__ int hough_select(const DevParams& P, const float* X, const int* szl, 
         const int lo = zlo(X + st, lz, n, fminf(xa, xb)), hi = zhi(X + st, lz, n, fmaxf(xa, xb));
         ull m = 0;
         for (int k = lo; k < hi; ++k) {
+            if (is_used(used, st + k)) continue;
             const float ty = (Xl - X[st + k]) * P.uinv_t[u] * P.uinv_z[u];
             const int b = min(max(__float2int_rd((ty - P.h_lo[h]) * P.h_inv_w), 0), P.h_bins - 1);
             m |= 1ull << b;
@@ -405,7 +414,7 @@ __device__ int hough_select(const DevParams& P, const float* X, const int* szl, 
 // step 2 for one t_y hypothesis: the closest hit within uv_tol in every
 // stereo layer (ties to the smaller x); stops once n_uv_min is out of reach.
 __device__ void uv_hough(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
-                         const float* Xs, float ty, UV& o) {
+                         const uint32_t* used, const float* Xs, float ty, UV& o) {
     int n = 0;
     o.n = 0;
 #pragma unroll
@@ -419,6 +428,7 @@ __device__ void uv_hough(const DevParams& P, const float* X, const int* szl, con
         for (; k < nn; ++k) {
             const float xh = xs[k];
             if (xh > xp + P.uv_tol) break;
+            if (is_used(used, st + k)) continue;
             const float d = fabsf(xh - xp);
             if (d <= P.uv_tol && (best < 0 || d < bd)) {
                 best = st + k;
@@ -544,7 +554,8 @@ size_t seed_slot_bytes(int cand_cap, int max_xhits) {
     return align16(sizeof(int) * 16 * size_t(cand_cap)) +
            sizeof(ull) * (size_t(max_xhits) + cand_cap + size_t(kTripPerCand) * cand_cap) +
            16 + (2 * sizeof(uint4) + sizeof(uint2)) * kUvStore + sizeof(float) * 6 * size_t(cand_cap) + 8 +
-           sizeof(ull) * kTripLocal * kMaxThreads + 9 * size_t(cand_cap);
+           sizeof(ull) * kTripLocal * kMaxThreads + 9 * size_t(cand_cap) + 4 +
+           sizeof(uint32_t) * ((size_t(max_xhits) + 31) / 32);
 }
 
 // Two instantiations: CTAs of up to 256 threads with five per SM (48
@@ -553,7 +564,9 @@ size_t seed_slot_bytes(int cand_cap, int max_xhits) {
 // two per SM (64 registers).
 constexpr int kSeedBlocks256 = 5;
 
-template <int kT, int kB>
+// kSeq: compiled with the HLT2-style pass loop and taken-hit checks; the HLT1
+// instantiation has neither (they fold away).
+template <int kT, int kB, bool kSeq>
 __global__ void __launch_bounds__(kT, kB)
 k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -604,6 +617,10 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     ull* tloc = reinterpret_cast<ull*>(g_xs + 6 * CC) + tid;
     uint8_t* hcl = reinterpret_cast<uint8_t*>(reinterpret_cast<ull*>(g_xs + 6 * CC) + kTripLocal * kMaxThreads);
     uint8_t* hn = hcl + 8 * CC;  // Hough variant: kept clusters per seed and their count
+    // HLT2-style mode: bits of the half's hits taken by earlier iterations
+    uint32_t* g_used = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(hn + CC) + 3) & ~uintptr_t(3));
+    constexpr bool seq = kSeq;
+    const uint32_t* used = kSeq ? g_used : nullptr;
     __shared__ int s_nvalid;
     int spar = 0;  // which half of tmp the next block scan uses
 
@@ -651,23 +668,48 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
         }
         __syncthreads();
 
-        // ------------------------------------------------------------ XZ
-        // Each round takes up to T first hits (iteration 0's T1 layer, then
-        // iteration 1's), expands their T3 windows into pairs, and each thread
-        // walks a contiguous range of the round's pairs twice: once to count
-        // its triplets, once (after a block scan) to write them in order into
-        // the round's triplet buffer; the triplets then become candidates.
-        int ncand = 0;
+        // HLT1: one pass over all iterations, then one clone kill and one UV
+        // step.  HLT2-style (seq): one pass per iteration, each with its own
+        // clone kill and UV step; the hits of a pass's seeds are marked in
+        // g_used before the next pass.  Candidates and kept seeds of all
+        // passes are appended to the same lists; the output step takes them
+        // all.
+        if (seq) {
+            for (int i = tid; i < (nh + 31) / 32; i += T) g_used[i] = 0u;
+        }
+        if (tid == 0) s_nvalid = 0;
+        __syncthreads();
+        int ncand = 0, nk = 0;
         bool overflow = false;
-        const int n1_0 = szl[P.it[0].s1 + 1] - szl[P.it[0].s1];
-        const int n1_1 = P.n_iter > 1 ? szl[P.it[1].s1 + 1] - szl[P.it[1].s1] : 0;
-        const int n_items = n1_0 + n1_1;
+        const bool hough = P.uv_mode == 1;
+        const int n_pass = seq ? P.n_iter : 1;
+        for (int ipass = 0; ipass < n_pass; ++ipass) {
+        const int it_lo = seq ? ipass : 0, it_hi = seq ? ipass + 1 : P.n_iter;
+        int n_items = 0;
+        for (int it = it_lo; it < it_hi; ++it) n_items += szl[P.it[it].s1 + 1] - szl[P.it[it].s1];
+        const int cb0 = ncand;
+        // ------------------------------------------------------------ XZ
+        // Each round takes up to T first hits (the pass's iterations' T1
+        // layers in order), expands their T3 windows into pairs, and each
+        // thread walks a contiguous range of the round's pairs (once into a
+        // small buffer; again only if a thread found more triplets than it
+        // holds), a block scan placing the triplets in order in the round's
+        // triplet buffer; the triplets then become candidates.
         for (int b1 = 0; b1 < n_items; b1 += T) {
             const int i = b1 + tid;
             int np = 0, lo3 = 0, tag = 0;
             if (i < n_items) {
-                const int it = i >= n1_0;
-                const int k1 = i - (it ? n1_0 : 0);
+                int it = it_lo, k1 = i;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    if (it + 1 < it_hi) {
+                        const int n1 = szl[P.it[it].s1 + 1] - szl[P.it[it].s1];
+                        if (k1 >= n1) {
+                            k1 -= n1;
+                            ++it;
+                        }
+                    }
+                }
                 const IterP& I = P.it[it];
                 const float x1 = X[szl[I.s1] + k1];
                 const float xc = I.scale3 * x1;
@@ -675,6 +717,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 const uint16_t* l3 = lut + I.s3 * kLutBins;
                 lo3 = zlo(X + st3, l3, n3, xc - I.dx3);
                 np = zhi(X + st3, l3, n3, xc + I.dx3) - lo3;
+                if (is_used(used, szl[I.s1] + k1)) np = 0;
                 tag = (it << 20) | k1;
             }
             ctr[0] += np;
@@ -710,14 +753,15 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                         x1 = X[szl[P.it[it].s1] + k1];
                     }
                     const IterP& I = P.it[it];
-                    int lo2;
-                    const int c = pair_window(P, I, X, szl, lut, x1, X[szl[I.s3] + k3], lo2);
+                    int lo2 = 0, c = 0;
+                    if (!is_used(used, szl[I.s3] + k3)) c = pair_window(P, I, X, szl, lut, x1, X[szl[I.s3] + k3], lo2);
                     for (int q = 0; q < c; ++q) {
+                        if (is_used(used, szl[I.s2] + lo2 + q)) continue;
                         const ull key = pack_trip(it, k1, k3, lo2 + q);
-                        if (direct) trip[wofs + w + q] = key;
-                        else if (w + q < kTripLocal) tloc[(w + q) * T] = key;
+                        if (direct) trip[wofs + w] = key;
+                        else if (w < kTripLocal) tloc[w * T] = key;
+                        ++w;
                     }
-                    w += c;
                     ++k3;
                 }
                 return w;
@@ -748,7 +792,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 if (t < ntrip) {
                     const ull tk = trip[t];
                     const int it = static_cast<int>(tk >> 60);
-                    code = do_triplet(P, P.it[it], X, szl, lut, sG, sMask, static_cast<int>((tk >> 40) & 0xFFFFF),
+                    code = do_triplet(P, P.it[it], X, szl, lut, sG, sMask, used, static_cast<int>((tk >> 40) & 0xFFFFF),
                                       static_cast<int>(tk & 0xFFFFF), static_cast<int>((tk >> 20) & 0xFFFFF), o);
                     ctr[2] += code >= 1;
                 }
@@ -772,23 +816,17 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 ncand += tot;
             }
         }
-        if (tid == 0) ctr[3] += ncand;
-
         if (overflow || ncand > CC) {
-            if (tid == 0) {
-                A.status[e] = -3;  // ST_OVERFLOW
-                A.item_count[item] = 0;
-            }
-            continue;
+            overflow = true;
+            break;
         }
-        const int nc = ncand;
 
         // ------------------------------------------------------------ clone kill
         const int nxh = szl[6];
         ull* tbl = nxh <= A.tbl_smem ? stab : g_tbl;
         for (int i = tid; i < nxh; i += T) tbl[i] = ~0ull;
         __syncthreads();
-        for (int k = tid; k < nc; k += T) {
+        for (int k = cb0 + tid; k < ncand; k += T) {
             const ull key = (ull(__float_as_uint(c_f[7 * CC + k])) << 32) | unsigned(k);
 #pragma unroll
             for (int s = 0; s < 6; ++s) {
@@ -797,11 +835,11 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             }
         }
         __syncthreads();
-        int nk = 0;
-        for (int b = 0; b < nc; b += T) {
+        const int kb = nk;
+        for (int b = cb0; b < ncand; b += T) {
             const int k = b + tid;
             int keep = 0;
-            if (k < nc) {
+            if (k < ncand) {
                 const ull key = (ull(__float_as_uint(c_f[7 * CC + k])) << 32) | unsigned(k);
                 int owned = 0;
 #pragma unroll
@@ -816,13 +854,17 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             if (keep) kept[nk + o] = k;
             nk += tot;
         }
-        if (tid == 0) ctr[4] += nk;
+        if (tid == 0) ctr[4] += nk - kb;
         __syncthreads();
 
         // ------------------------------------------------------------ UV
-        ull* ukey = nk <= A.key_smem ? skey : g_key;
-        float* Xs = nk <= A.key_smem ? sXs : g_xs;
-        for (int j = tid; j < nk; j += T) {
+        // (kept seeds [kb, nk) of this pass; with several passes the keys and
+        // stereo positions live in global scratch)
+        ull* ukey = (!seq && nk <= A.key_smem) ? skey : g_key;
+        float* Xs = (!seq && nk <= A.key_smem) ? sXs : g_xs;
+        const int nkp = nk - kb;
+        const int nvs0 = min(s_nvalid, kUvStore);
+        for (int j = kb + tid; j < nk; j += T) {
             ukey[j] = ~0ull;
             const int k = kept[j];
             const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
@@ -830,24 +872,23 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
 #pragma unroll
             for (int u = 0; u < 6; ++u) Xs[6 * j + u] = x_at_uv(P, th, dth, u);
         }
-        if (tid == 0) s_nvalid = 0;
         __syncthreads();
-        const bool hough = P.uv_mode == 1;
         if (hough) {
-            for (int j = tid; j < nk; j += T) hn[j] = static_cast<uint8_t>(hough_select(P, X, szl, lut, Xs + 6 * j, h, hcl + 8 * j));
+            for (int j = kb + tid; j < nk; j += T)
+                hn[j] = static_cast<uint8_t>(hough_select(P, X, szl, lut, used, Xs + 6 * j, h, hcl + 8 * j));
             __syncthreads();
         }
         // iterative: one item per (seed, pass), numbered pass-major (all pass
         // A chains, then pass B) so that a warp's chains mostly share their
         // initial layer; Hough: one item per seed with its hypotheses
-        const int nuv = hough ? nk : 2 * nk;
+        const int nuv = hough ? nkp : 2 * nkp;
         for (int b = 0; b < nuv; b += T) {
             const int i = b + tid;
             int cntc = 0, lo = 0;
             if (i < nuv && hough) {
-                cntc = hn[i] * P.h_fine;
+                cntc = hn[kb + i] * P.h_fine;
             } else if (i < nuv) {
-                const int pass = i >= nk, j = i - (pass ? nk : 0);
+                const int pass = i >= nkp, j = kb + i - (pass ? nkp : 0);
                 const int ui = P.uv_init[pass];
                 const float Xi = Xs[6 * j + ui];
                 const float t = P.ut[ui];
@@ -877,13 +918,16 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                         kinit = sA[o];
                     }
                     const int i2 = sB[o];
-                    const int pass = hough ? 0 : i2 >= nk, j = i2 - (pass ? nk : 0);
+                    const int pass = hough ? 0 : i2 >= nkp, j = kb + i2 - (pass ? nkp : 0);
                     UV u;
                     if (hough) {
                         const int r = kinit / P.h_fine;
-                        uv_hough(P, X, szl, lut, Xs + 6 * j, hough_ty(P, h, hcl[8 * j + r], kinit - r * P.h_fine), u);
+                        uv_hough(P, X, szl, lut, used, Xs + 6 * j, hough_ty(P, h, hcl[8 * j + r], kinit - r * P.h_fine),
+                                 u);
+                    } else if (is_used(used, szl[6 + P.uv_init[pass]] + kinit)) {
+                        u.n = 0;  // initial hit taken by an earlier iteration
                     } else {
-                        uv_chain(P, X, szl, lut, Xs + 6 * j, pass, kinit, u);
+                        uv_chain(P, X, szl, lut, used, Xs + 6 * j, pass, kinit, u);
                     }
                     if (u.n >= P.n_uv_min) {
                         ++ctr[6];
@@ -912,7 +956,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
         }
         // the stored chains' fits, one per thread
         const int nvs = min(s_nvalid, kUvStore);
-        for (int q = tid; q < nvs; q += T) {
+        for (int q = nvs0 + tid; q < nvs; q += T) {
             const uint4 v = vstore[q];
             const uint2 mt = vmeta[q];
             const unsigned w[3] = {v.x, v.y, v.z};
@@ -933,6 +977,45 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             atomicMin(&ukey[j], uv_key(u.n, u.chi2, static_cast<int>(mt.y & 1u), static_cast<int>(mt.y >> 1), q));
         }
         __syncthreads();
+        if (seq && ipass + 1 < n_pass) {
+            // hit cleanup: this pass's seeds give their hits to no later pass.
+            // Their stereo hits come from the chain store; a pass whose store
+            // overflowed cannot be cleaned up and counts as an overflow.
+            if (s_nvalid > kUvStore) {
+                overflow = true;
+                break;
+            }
+            for (int j = kb + tid; j < nk; j += T) {
+                const ull key = ukey[j];
+                if (key == ~0ull) continue;
+                const int k = kept[j];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const int p = c_pos[q * CC + k];
+                    if (p >= 0) atomicOr(&g_used[p >> 5], 1u << (p & 31));
+                }
+                const uint4 v = vstore[key & 0x1FFFu];
+                const unsigned w[3] = {v.x, v.y, v.z};
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const int p = static_cast<int>((w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu) - 1;
+                    if (p >= 0) atomicOr(&g_used[p >> 5], 1u << (p & 31));
+                }
+            }
+            __syncthreads();
+        }
+        }  // passes
+        if (tid == 0) ctr[3] += ncand;
+        if (overflow || (seq && s_nvalid > kUvStore)) {
+            if (tid == 0) {
+                A.status[e] = -3;  // ST_OVERFLOW
+                A.item_count[item] = 0;
+            }
+            continue;
+        }
+        ull* ukey = (!seq && nk <= A.key_smem) ? skey : g_key;
+        float* Xs = (!seq && nk <= A.key_smem) ? sXs : g_xs;
+
 
         // ------------------------------------------------------------ seeds
         int nseed = 0;
@@ -990,9 +1073,10 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     const int kinit = static_cast<int>((key >> 13) & 0xFFFFu);
                     if (P.uv_mode == 1) {
                         const int r = kinit / P.h_fine;
-                        uv_hough(P, X, szl, lut, Xs + 6 * j, hough_ty(P, h, hcl[8 * j + r], kinit - r * P.h_fine), u);
+                        uv_hough(P, X, szl, lut, used, Xs + 6 * j, hough_ty(P, h, hcl[8 * j + r], kinit - r * P.h_fine),
+                                 u);
                     } else {
-                        uv_chain(P, X, szl, lut, Xs + 6 * j, static_cast<int>((key >> 29) & 1), kinit, u);
+                        uv_chain(P, X, szl, lut, used, Xs + 6 * j, static_cast<int>((key >> 29) & 1), kinit, u);
                     }
                     uv_fit(P, X, th, dth, u);
                 }
@@ -1428,8 +1512,12 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
 // Raise each kernel's dynamic shared-memory ceiling to what the device allows
 // next to the kernel's own static shared memory (opt-in maximum - static).
 cudaError_t set_smem_limits(size_t optin) {
-    const void* fns[] = {reinterpret_cast<const void*>(k_build), reinterpret_cast<const void*>(k_seed<256, kSeedBlocks256>),
-                         reinterpret_cast<const void*>(k_seed<kMaxThreads, 2>), reinterpret_cast<const void*>(k_match)};
+    const void* fns[] = {reinterpret_cast<const void*>(k_build),
+                         reinterpret_cast<const void*>(k_seed<256, kSeedBlocks256, false>),
+                         reinterpret_cast<const void*>(k_seed<kMaxThreads, 2, false>),
+                         reinterpret_cast<const void*>(k_seed<256, kSeedBlocks256, true>),
+                         reinterpret_cast<const void*>(k_seed<kMaxThreads, 2, true>),
+                         reinterpret_cast<const void*>(k_match)};
     for (const void* f : fns) {
         cudaFuncAttributes fa;
         cudaError_t err = cudaFuncGetAttributes(&fa, f);
@@ -1449,9 +1537,9 @@ int build_blocks_per_sm(int threads, size_t smem) {
 int seed_blocks_per_sm(int threads, size_t smem) {
     int n = 0;
     if (threads <= 256)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed<256, kSeedBlocks256>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed<256, kSeedBlocks256, false>, threads, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed<kMaxThreads, 2>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed<kMaxThreads, 2, false>, threads, smem);
     return n;
 }
 int match_blocks_per_sm(int threads, size_t smem) {
@@ -1467,10 +1555,14 @@ cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int t
 
 cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s) {
     const size_t smem = seed_smem_bytes(threads, a.smem_hits, a.tbl_smem, a.key_smem);
-    if (threads <= 256)
-        k_seed<256, kSeedBlocks256><<<grid, threads, smem, s>>>(P, a);
-    else
-        k_seed<kMaxThreads, 2><<<grid, threads, smem, s>>>(P, a);
+    const bool sq = P.iter_mode == 1;
+    if (threads <= 256) {
+        if (sq) k_seed<256, kSeedBlocks256, true><<<grid, threads, smem, s>>>(P, a);
+        else k_seed<256, kSeedBlocks256, false><<<grid, threads, smem, s>>>(P, a);
+    } else {
+        if (sq) k_seed<kMaxThreads, 2, true><<<grid, threads, smem, s>>>(P, a);
+        else k_seed<kMaxThreads, 2, false><<<grid, threads, smem, s>>>(P, a);
+    }
     return cudaGetLastError();
 }
 
