@@ -372,6 +372,8 @@ def main():
             st, dict(zmx=zmx, iter_mode=1, n_iter=3, p_min_iter=[5000.0, 3000.0, 1500.0], **tuned), db, out, cap,
             n_ev, flush, stream, args.steps)
         log(f"iterations_hlt2: {result['iterations_hlt2']}")
+        result["uneven_batched"] = time_uneven(st, cfg, local, flush, stream, args.steps)
+        log(f"uneven_batched: {result['uneven_batched']}")
         graph.st_graph_launch(stream)  # the default configuration's outputs again
         stream.synchronize()
         result["ut"] = time_ut(st, ctx, db, out, flush, stream, args.steps)
@@ -518,6 +520,44 @@ def time_variant(st, overrides, db, out, cap, n_ev, flush, stream, steps, nn=Non
     return {"value": n_ev * steps / (tot / 1000.0), "unit": "events/s", "ms_per_step": tot / steps,
             "kernel_ms": kms, "seeds_per_event": seeds / n_ev,
             "config": {k: v for k, v in overrides.items() if k != "zmx"}}
+
+
+def time_uneven(st, cfg, local, flush, stream, steps):
+    """The uneven-occupancy batch (10 000 events, log-normal track counts,
+    100-15 000 hits per event) as one persistent graph launch."""
+    import torch
+    from synth import make_workload
+    b = make_workload("uneven")
+    dev = torch.device("cuda", local)
+    db = st.DeviceBatch.from_synth(b, device=dev)
+    cap = max(1024, b.n_hits // 4)
+    out = st.DeviceOutputs(b.n_events, cap, device=dev)
+    ctx = st.Context(cfg, device=local)
+    ctx.st_reserve(b.n_events, b.n_events * db.max_hits, db.max_hits, cap)
+    ctx.st_set_timing(True)
+    g = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
+    kms = {}
+    n = max(3, steps // 4)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            g.st_graph_launch(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(n):
+            flush.fill_(1)
+            e0.record(stream)
+            g.st_graph_launch(stream)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+            for k, v in ctx.st_kernel_ms().items():
+                kms[k] = kms.get(k, 0.0) + v / n
+    ok = int((out.status[: b.n_events] == 0).sum())
+    g.close()
+    ctx.close()
+    return {"value": b.n_events * n / (tot / 1000.0), "unit": "events/s", "ms_per_step": tot / n,
+            "events": b.n_events, "hits_per_event": b.n_hits / b.n_events,
+            "max_hits_per_event": int(np.max(np.diff(b.ev_off))), "events_ok": ok, "kernel_ms": kms}
 
 
 def time_ut(st, ctx, db, out, flush, stream, steps):
