@@ -222,11 +222,15 @@ int st_reserve(st_ctx* ctx, int64_t n_events, int64_t n_hits, int32_t max_hits_p
                int64_t seeds_cap);
 
 /* SciFi Seeding (Section 3): per event, hit containers sorted by (layer
- * zone, x); two XZ iterations of two-hit (Eqs. tolHp, alphacorr) and
- * three-hit (Section 3.3.3) searches; extension to the other x-layers
- * (1 mm) keeping >= 5 hits; least-squares x-z fit with d_ratio fixed and a
- * chi2/ndf cut; O(n) clone killing (Eq. seed_clone_score and the two-pass
- * vote of Section 3.3.4); iterative UV seeding (Section 3.4).
+ * zone, x); XZ iterations of two-hit (Eqs. tolHp, alphacorr) and three-hit
+ * (Section 3.3.3) searches; extension to the other x-layers (1 mm) keeping
+ * >= 5 hits; least-squares x-z fit with d_ratio fixed and a chi2/ndf cut;
+ * O(n) clone killing (Eq. seed_clone_score and the two-pass vote of Section
+ * 3.3.4); UV seeding (Section 3.4, iterative or Hough clusters by uv_mode).
+ * iter_mode 0 (HLT1): the iterations run independently and one clone kill
+ * follows; iter_mode 1: each iteration in turn with its own clone kill and
+ * UV step, the hits of its seeds removed before the next (an event whose
+ * store of UV combinations overflows in this mode gets ST_OVERFLOW).
  * Output `seeds` as described at st_seeds.  Returns ST_EINVAL for a bad
  * argument (NULL array, cap < 0, n_events < 0), ST_ENOMEM / ST_ECUDA for
  * allocation or launch failures; per-event problems go to seeds->status.
