@@ -135,9 +135,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source."""
+def profile_record(kernel):
+    """The committed ncu record of `kernel` (DRAM bytes and warp instructions
+    per launch), if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -145,10 +145,15 @@ def traffic_from_profile(kernel):
         d = json.load(open(p))
         e = d.get(kernel)
         if e and e.get("source_hash") == kernel_source_hash() and e.get("workload") == WORKLOAD:
-            return float(e["bytes_per_launch"])
+            return e
     except Exception:
         pass
     return None
+
+
+def traffic_from_profile(kernel):
+    e = profile_record(kernel)
+    return float(e["bytes_per_launch"]) if e else None
 
 
 # ---------------------------------------------------------------------------
@@ -223,8 +228,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--serve-seconds", type=float, default=6.0)
-    ap.add_argument("--serve-events", type=int, default=200000, help="bound on served events per rate")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-events", type=int, default=1000000, help="bound on served events per rate")
     ap.add_argument("--serve-rates", default="0.25,0.5,0.75,0.9,1.1",
                     help="offered rates as fractions of the batched capacity on the serving pool")
     ap.add_argument("--per-event", type=int, default=200, help="events timed with per-event launches")
@@ -357,6 +362,15 @@ def main():
     alg_bytes = 8.0 * batch.n_hits + 98.0 * counters["seeds"] / steps
     result["roofline"]["hbm"]["algorithmic_bytes"] = alg_bytes
     result["roofline"]["hbm"]["achieved_gbs"] = alg_bytes / (seed_ms / 1000.0) / 1e9 if seed_ms > 0 else 0.0
+    # instruction-issue view of the same launch: warp instructions (ncu, same
+    # kernel source) over the live launch time against 4 issue slots per SM
+    rec = profile_record("k_seed")
+    if rec and rec.get("warp_instructions") and seed_ms > 0:
+        issue_peak = N_SMS * 4 * sm_mhz * 1e6
+        achieved_issue = rec["warp_instructions"] / (seed_ms / 1000.0)
+        result["roofline"]["issue"] = {"warp_instructions_per_launch": rec["warp_instructions"],
+                                       "achieved_per_s": achieved_issue, "peak_per_s": issue_peak,
+                                       "frac": achieved_issue / issue_peak}
 
     # ---------------- the Hough-cluster UV variant on the same batch
     if not args.no_variants:
