@@ -22,8 +22,6 @@ namespace st {
 
 typedef unsigned long long ull;
 
-__constant__ int kXLayer[6] = {0, 3, 4, 7, 8, 11};
-__constant__ int kULayer[6] = {1, 2, 5, 6, 9, 10};
 
 static __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
@@ -1080,30 +1078,33 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     }
                     uv_fit(P, X, th, dth, u);
                 }
-                int32_t* ho = A.pool_hits + r * 12;
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
+                // the record goes out as 16-byte stores (pool rows are 48 /
+                // 32 / 16 bytes long and the pool is 256-byte aligned)
+                // layers 0..11 are x u v x | x u v x | x u v x: x slot q and
+                // stereo slot q in layer order
+                auto hx = [&](int q) {
                     const int p = c_pos[q * CC + k];
-                    ho[kXLayer[q]] = p >= 0 ? A.corig[cbh + p] : -1;
-                    const int qq = u.pos[q];
-                    ho[kULayer[q]] = qq >= 0 ? A.corig[cbh + qq] : -1;
-                }
+                    return p >= 0 ? A.corig[cbh + p] : -1;
+                };
+                auto hu = [&](int q) { return u.pos[q] >= 0 ? A.corig[cbh + u.pos[q]] : -1; };
+                int4* ho = reinterpret_cast<int4*>(A.pool_hits + r * 12);
+                ho[0] = make_int4(hx(0), hu(0), hu(1), hx(1));
+                ho[1] = make_int4(hx(2), hu(2), hu(3), hx(3));
+                ho[2] = make_int4(hx(4), hu(4), hu(5), hx(5));
                 const float a = th[0] + dth[0], bb = th[1] + dth[1], cc = th[2] + dth[2];
                 // y(z) = tyr z + wm + beta (z - zc - zm)
                 const float ty = u.tyr + u.beta;
                 const float y0 = fmaf(-u.beta, P.zc_uv + u.zm, u.wm);
                 const float yS = fmaf(u.tyr, P.zS, fmaf(u.beta, (P.zS - P.zc_uv) - u.zm, u.wm));
-                float* po = A.pool_params + r * 8;
-                po[0] = a; po[1] = bb; po[2] = cc; po[3] = c_f[6 * CC + k];
-                po[4] = y0; po[5] = ty; po[6] = u.chi2; po[7] = 0.f;
-                float* so = A.pool_state + r * 4;
-                so[0] = fmaf(th[2], P.fS, fmaf(th[1], P.zbS, th[0])) +
-                        fmaf(dth[2], P.fS, fmaf(dth[1], P.zbS, dth[0]));
-                so[1] = yS;
-                so[2] = fmaf(cc, P.dfS, bb);
-                so[3] = ty;
-                A.pool_n[r * 2] = static_cast<int8_t>(c_nx[k]);
-                A.pool_n[r * 2 + 1] = static_cast<int8_t>(u.n);
+                float4* po = reinterpret_cast<float4*>(A.pool_params + r * 8);
+                po[0] = make_float4(a, bb, cc, c_f[6 * CC + k]);
+                po[1] = make_float4(y0, ty, u.chi2, 0.f);
+                reinterpret_cast<float4*>(A.pool_state)[r] =
+                    make_float4(fmaf(th[2], P.fS, fmaf(th[1], P.zbS, th[0])) +
+                                    fmaf(dth[2], P.fS, fmaf(dth[1], P.zbS, dth[0])),
+                                yS, fmaf(cc, P.dfS, bb), ty);
+                const unsigned short nn = static_cast<unsigned short>((c_nx[k] & 0xFF) | ((u.n & 0xFF) << 8));
+                reinterpret_cast<unsigned short*>(A.pool_n)[r] = nn;
             }
             wbase += tot;
         }
