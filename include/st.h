@@ -383,7 +383,10 @@ int st_pipeline_configure(st_ctx* ctx, const st_pipeline_config* pc);
  * launch on a free slot; slots run on their own streams and overlap on the
  * device.  *ticket identifies the batch.  ST_OVERFLOW if the batch can never
  * fit a slot; ST_ESTATE after st_destroy has begun.  Results stay in a device
- * output ring until polled: poll every ticket. */
+ * output ring until polled: poll every ticket.  A launch runs seeding_run and
+ * matching_run with the context's configuration (so also the final
+ * selection when final_sel is set); UT hits are not part of the pipeline
+ * (ut_run on device buffers). */
 int pipeline_submit(st_ctx* ctx, const st_hits* host_hits, const st_velo* host_velo,
                     uint64_t* ticket);
 
