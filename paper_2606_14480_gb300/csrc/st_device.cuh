@@ -212,6 +212,36 @@ __device__ __forceinline__ int block_exscan1(int v, int* buf, int& par, int& tot
     return x - v + before;
 }
 
+// block_exscan1 that also returns whether any thread's flag was set (the
+// flag rides in bit 30 of the warp partials; the values must stay below 2^30).
+__device__ __forceinline__ int block_exscan1_any(int v, bool flag, int* buf, int& par, int& total, bool& any) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    int* t = buf + (par ? 17 : 0);
+    par ^= 1;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const int f = __any_sync(0xffffffffu, flag) ? (1 << 30) : 0;
+    if (lane == 31) t[wid] = x | f;
+    __syncthreads();
+    const int tw = lane < nw ? t[lane] : 0;
+    int w = tw & ((1 << 30) - 1);
+    int before = lane < wid ? w : 0;
+    const bool fa = __any_sync(0xffffffffu, (tw >> 30) & 1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+    }
+    total = w;
+    any = fa;
+    return x - v + before;
+}
+
 __device__ __forceinline__ int warp_sum(int v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -6,13 +6,16 @@
 //             slot, x, index) with a bucketed rank sort in shared memory, write
 //             the per-event container (x, original index) and slot offsets.
 //   k_seed    one detector half of one event per item (the paper keeps the
-//             halves apart, Section 5.2): XZ seeding of both iterations with
+//             halves apart, Section 5.2): XZ seeding of the iterations with
 //             load-balanced expansion of pairs and triplets, extension and
 //             compensated least-squares fit, O(n) clone killing with a 64-bit
-//             atomicMin table, iterative UV seeding with a 64-bit atomicMin
-//             per seed, and the seed records.
+//             atomicMin table, UV seeding (iterative or Hough clusters) with a
+//             64-bit atomicMin per seed, and the seed records; HLT2-style
+//             iterations run as passes with a taken-hit bitmask.
 //   k_scan / k_gather   per-event CSR of the seed records.
-//   k_match   one event per item: VELO x seed grid, warp argmin per seed.
+//   k_match   one event per item: VELO segments bucketed by ty in shared
+//             memory, one thread per seed for its lowest chi2_match, then
+//             optionally the final selection (ghost network, clones).
 #include <algorithm>
 #include <cfloat>
 
@@ -765,9 +768,9 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 return w;
             };
             const int nt = walk(false, 0);
-            const int again = __syncthreads_or(nt > kTripLocal);
             int tot_t;
-            int wofs = block_exscan1(nt, tmp, spar, tot_t);
+            bool again;
+            int wofs = block_exscan1_any(nt, nt > kTripLocal, tmp, spar, tot_t, again);
             ctr[1] += nt;
             if (ntrip + tot_t > TC) overflow = true;
             if (!overflow) {
@@ -1275,6 +1278,9 @@ __device__ float ghost_nn(const DevParams& P, const float f[8]) {
 // bucketed by ty, so a seed only visits the buckets its |dty| cut can reach
 // (every other pair fails that cut).  Events with more segments than fit are
 // processed in chunks, each scanned in full.
+// kFinal: compiled with the final selection of Section 4.4 (the plain
+// instantiation does not carry its registers).
+template <bool kFinal>
 __global__ void __launch_bounds__(kMaxThreads)
 k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1430,7 +1436,7 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
             }
             __syncthreads();
         }
-        if (P.final_sel) {
+        if (kFinal && P.final_sel) {
             // Section 4.4: ghost probability of each best pair and the cut
             for (int s = tid; s < ns; s += T) {
                 const int v = A.velo_idx[s0 + s];
@@ -1518,7 +1524,7 @@ cudaError_t set_smem_limits(size_t optin) {
                          reinterpret_cast<const void*>(k_seed<kMaxThreads, 2, false>),
                          reinterpret_cast<const void*>(k_seed<256, kSeedBlocks256, true>),
                          reinterpret_cast<const void*>(k_seed<kMaxThreads, 2, true>),
-                         reinterpret_cast<const void*>(k_match)};
+                         reinterpret_cast<const void*>(k_match<false>), reinterpret_cast<const void*>(k_match<true>)};
     for (const void* f : fns) {
         cudaFuncAttributes fa;
         cudaError_t err = cudaFuncGetAttributes(&fa, f);
@@ -1545,7 +1551,7 @@ int seed_blocks_per_sm(int threads, size_t smem) {
 }
 int match_blocks_per_sm(int threads, size_t smem) {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_match, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_match<false>, threads, smem);
     return n;
 }
 
@@ -1584,7 +1590,10 @@ cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_match(const DevParams& P, const MatchArgs& a, int grid, int threads, cudaStream_t s) {
-    k_match<<<grid, threads, match_smem_bytes(a.velo_smem), s>>>(P, a);
+    if (P.final_sel)
+        k_match<true><<<grid, threads, match_smem_bytes(a.velo_smem), s>>>(P, a);
+    else
+        k_match<false><<<grid, threads, match_smem_bytes(a.velo_smem), s>>>(P, a);
     return cudaGetLastError();
 }
 
