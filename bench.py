@@ -9,7 +9,7 @@ flushed (256 MB write) between timed steps, outside the timed interval.
 
 Reported beside the batched number (one JSON line on stdout):
   e2e           the same batch through pipeline_submit / pipeline_poll with
-                host buffers (copies in the timed region), two batches in flight
+                host buffers (copies in the timed region), three batches in flight
   per_event     the plain per-event launch: seeding_run + matching_run per
                 event on one stream
   served        continuous batching of a Poisson request stream (batch sizes
@@ -402,7 +402,7 @@ def main():
 
     # ---------------- e2e through the public host API (pipeline)
     ctx2 = st.Context(cfg, device=local)
-    ctx2.st_pipeline_configure(n_slots=2, max_events_per_slot=n_ev, max_hits_per_slot=batch.n_hits + 16,
+    ctx2.st_pipeline_configure(n_slots=3, max_events_per_slot=n_ev, max_hits_per_slot=batch.n_hits + 16,
                                max_hits_per_event=db.max_hits, max_velo_per_event=1024,
                                max_velo_per_slot=int(batch.velo.shape[0]) + 16)
     hh, hv, keep = st.HostBuffers.inputs(batch.ev_off, batch.x, batch.zone, batch.velo_off, batch.velo)
@@ -412,9 +412,9 @@ def main():
         rc, _ = ctx2.pipeline_poll(t, hb.seeds, hb.long, 60_000_000)
         assert rc == st.ST_OK, rc
     h2d = 8 * (n_ev + 1) * 2 + 8 * batch.n_hits + 16 * batch.velo.shape[0]
-    # two batches in flight: the next batch's inputs are copied in while the
+    # three batches in flight: the next batches' inputs are copied in while the
     # current one runs; every step's results are read back to the host
-    depth = 2
+    depth = 3
     pending = []
     if ws > 1:
         torch.distributed.barrier()
@@ -434,7 +434,7 @@ def main():
     log(f"e2e: {1000 * e2e_total / args.steps:.3f} ms/step")
     result["e2e"] = {"value": job_rate(n_ev * args.steps, ws, e2e_total), "unit": "events/s",
                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                     "api": "pipeline_submit + pipeline_poll, pageable host buffers, two batches in flight"}
+                     "api": "pipeline_submit + pipeline_poll, pageable host buffers, three batches in flight"}
 
     if rank == 0 and ws == 1:
         # ---------------- plain per-event launch
