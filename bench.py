@@ -291,7 +291,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     graph = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    kernels_per_step = 5  # build, seed, scan, gather, match
+    kernels_per_step = 6  # build, order, seed, scan, gather, match
 
     # ---------------- batched: graph replay, inputs resident in HBM
     with torch.cuda.stream(stream):

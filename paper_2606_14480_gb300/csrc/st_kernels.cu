@@ -5,6 +5,8 @@
 //   k_build   one event per item: validate hits, sort them by (container
 //             slot, x, index) with a bucketed rank sort in shared memory, write
 //             the per-event container (x, original index) and slot offsets.
+//   k_order   one CTA: the seeding items sorted by cost class, costliest
+//             first, the order in which k_seed's queue hands them out.
 //   k_seed    one detector half of one event per item (the paper keeps the
 //             halves apart, Section 5.2): XZ seeding of the iterations with
 //             load-balanced expansion of pairs and triplets, extension and
@@ -59,12 +61,32 @@ __device__ __forceinline__ void flush_counters(unsigned long long* dst, const ul
 
 constexpr float kBinRange = 3500.f;
 
+// Seeding items are handed out costliest first (largest-processing-time
+// order), so that no large item starts when the rest of the batch is nearly
+// done.  The cost of a (event, half) item is the size of its two-hit search
+// domain, sum over iterations of n(T1) n(T3), plus its hit count; its class
+// is that cost on a quarter-octave scale.
+constexpr int kCostClasses = 128;
+static_assert(kCostClasses % 32 == 0, "one warp scans the classes");
+
+__device__ __forceinline__ int cost_class(ull cost) {
+    if (cost < 4u) return static_cast<int>(cost);
+    const int oct = 63 - __clzll(static_cast<long long>(cost));
+    return min(4 * oct + static_cast<int>((cost >> (oct - 2)) & 3u), kCostClasses - 1);
+}
+
+__device__ __forceinline__ void set_item_class(const BuildArgs& A, int64_t item, int c) {
+    A.item_class[item] = c;
+    atomicAdd(A.class_count + c, 1);
+}
+
 size_t build_smem_bytes(int bins, int smem_hits) {
     const int NB = kZones * bins;
     return align16(sizeof(int) * (2 * NB + 1 + 36)) + align16(size_t(10) * smem_hits);
 }
 
-__global__ void __launch_bounds__(kMaxThreads)
+// at most 40 registers: three 512-thread CTAs per SM
+__global__ void __launch_bounds__(kMaxThreads, 3)
 k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = A.bins, NB = kZones * B, T = blockDim.x, tid = threadIdx.x;
@@ -87,6 +109,7 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
         if (n64 < 0 || n64 > A.max_hits) {
             for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
             if (tid == 0) A.status[e] = -3;  // ST_OVERFLOW
+            if (tid < 2) set_item_class(A, 2 * e + tid, 0);
             continue;
         }
         const int n = static_cast<int>(n64);
@@ -94,6 +117,7 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
         if (cb + n > A.cont_cap) {  // an earlier oversized event pushed this one past the container
             for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
             if (tid == 0) A.status[e] = -3;  // ST_OVERFLOW
+            if (tid < 2) set_item_class(A, 2 * e + tid, 0);
             continue;
         }
         const bool in_smem = n <= A.smem_hits;
@@ -107,30 +131,45 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
         if (tid == 0) s_bad = 0;
         __syncthreads();
         const float binscale = B / (2.f * kBinRange);
-        for (int i = tid; i < n; i += T) {
-            const float x = A.x[h0 + i];
-            const int zn = A.zone[h0 + i];
-            bool bad = !(zn >= 0 && zn < kZones) || !isfinite(x);
-            if (!bad) {
-                const int L = zn >> 1;
-                if (A.z && !(fabsf(A.z[h0 + i] - P.zl[L]) <= 1e-3f)) bad = true;
-                if (A.dxdy && !(fabsf(A.dxdy[h0 + i] - P.tl[L]) <= 1e-6f)) bad = true;
+        // four hits per thread per round, their loads issued together
+        for (int i0 = tid; i0 < n; i0 += 4 * T) {
+            float xs[4];
+            int zs[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + q * T;
+                xs[q] = i < n ? A.x[h0 + i] : 0.f;
+                zs[q] = i < n ? A.zone[h0 + i] : 0;
             }
-            if (bad) {
-                s_bad = 1;
-                continue;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + q * T;
+                if (i >= n) break;
+                const float x = xs[q];
+                const int zn = zs[q];
+                bool bad = !(zn >= 0 && zn < kZones) || !isfinite(x);
+                if (!bad) {
+                    const int L = zn >> 1;
+                    if (A.z && !(fabsf(A.z[h0 + i] - P.zl[L]) <= 1e-3f)) bad = true;
+                    if (A.dxdy && !(fabsf(A.dxdy[h0 + i] - P.tl[L]) <= 1e-6f)) bad = true;
+                }
+                if (bad) {
+                    s_bad = 1;
+                    continue;
+                }
+                int bin = __float2int_rd((x + kBinRange) * binscale);
+                bin = min(max(bin, 0), B - 1);
+                const int b = P.slot_of_zone[zn] * B + bin;
+                hx[i] = x;
+                bk[i] = static_cast<uint16_t>(b);
+                rk[i] = static_cast<uint16_t>(atomicAdd(&cnt[b], 1));
             }
-            int bin = __float2int_rd((x + kBinRange) * binscale);
-            bin = min(max(bin, 0), B - 1);
-            const int b = P.slot_of_zone[zn] * B + bin;
-            hx[i] = x;
-            bk[i] = static_cast<uint16_t>(b);
-            rk[i] = static_cast<uint16_t>(atomicAdd(&cnt[b], 1));
         }
         __syncthreads();
         if (s_bad) {
             for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
             if (tid == 0) A.status[e] = -1;  // ST_EINVAL
+            if (tid < 2) set_item_class(A, 2 * e + tid, 0);
             continue;
         }
         {   // exclusive scan of the bucket counts
@@ -162,6 +201,12 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
             A.corig[cb + s + r] = i;
         }
         for (int k = tid; k < kZoffStride; k += T) zo[k] = off[k * B];
+        if (tid < 2) {
+            auto nz = [&](int sl) { return ull(off[(sl + 1) * B] - off[sl * B]); };
+            ull cost = ull(off[(12 * tid + 12) * B] - off[12 * tid * B]);
+            for (int it = 0; it < P.n_iter; ++it) cost += nz(12 * tid + P.it[it].s1) * nz(12 * tid + P.it[it].s3);
+            set_item_class(A, 2 * e + tid, cost_class(cost));
+        }
         if (tid == 0) {
             A.status[e] = 0;
             ctr[0] += n;
@@ -169,6 +214,55 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
         }
     }
     flush_counters(A.counters + C_HITS, ctr, 2);
+}
+
+// The seeding items in cost order (a counting sort by class, costliest class
+// first), after k_build has counted the classes.  One thread per item; a
+// CTA's items of one class take consecutive places from one global atomic.
+// The order inside a class does not matter: items are independent and their
+// results are gathered per event.
+constexpr int kOrderThreads = 1024;
+
+__global__ void __launch_bounds__(kOrderThreads) k_order(const __grid_constant__ BuildArgs A) {
+    __shared__ int pos[kCostClasses], s_cnt[kCostClasses];
+    const int tid = threadIdx.x;
+    const unsigned lane = tid & 31;
+    if (tid < 32) {  // first place of each class: exclusive scan from the top class down
+        constexpr int kPer = kCostClasses / 32;
+        int c[kPer], t = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            c[q] = A.class_count[kCostClasses - 1 - (kPer * tid + q)];
+            t += c[q];
+        }
+        int x = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (tid >= o) x += y;
+        }
+        int run = x - t;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            pos[kCostClasses - 1 - (kPer * tid + q)] = run;
+            run += c[q];
+        }
+    }
+    for (int k = tid; k < kCostClasses; k += kOrderThreads) s_cnt[k] = 0;
+    __syncthreads();
+    const int64_t items = 2 * A.n_events;
+    const int64_t i = int64_t(blockIdx.x) * kOrderThreads + tid;
+    const int c = i < items ? A.item_class[i] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(same) - 1;
+    int r = 0;
+    if (c >= 0 && static_cast<int>(lane) == leader) r = atomicAdd(&s_cnt[c], __popc(same));
+    r = __shfl_sync(0xffffffffu, r, leader) + __popc(same & ((1u << lane) - 1u));
+    __syncthreads();
+    for (int k = tid; k < kCostClasses; k += kOrderThreads)
+        if (s_cnt[k]) pos[k] += atomicAdd(A.class_fill + k, s_cnt[k]);
+    __syncthreads();
+    if (c >= 0) A.order[pos[c] + r] = static_cast<int32_t>(i);
 }
 
 // ===========================================================================
@@ -629,7 +723,10 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_item = atomicAdd(A.queue, 1);
+        if (tid == 0) {
+            const int q = atomicAdd(A.queue, 1);
+            s_item = q < 2 * A.n_events ? A.order[q] : q;
+        }
         __syncthreads();
         const int64_t item = s_item;
         if (item >= 2 * A.n_events) break;
@@ -645,7 +742,16 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
         if (tid <= 12) szl[tid] = zo[tid] - zo[0];
         const float* X = A.cx + cbh;
         if (nh <= A.smem_hits) {
-            for (int i = tid; i < nh; i += T) sx[i] = X[i];
+            // four loads per thread in flight
+            int i = tid;
+            for (; i + 3 * T < nh; i += 4 * T) {
+                const float a0 = X[i], a1 = X[i + T], a2 = X[i + 2 * T], a3 = X[i + 3 * T];
+                sx[i] = a0;
+                sx[i + T] = a1;
+                sx[i + 2 * T] = a2;
+                sx[i + 3 * T] = a3;
+            }
+            for (; i < nh; i += T) sx[i] = X[i];
             X = sx;
         }
         __syncthreads();
@@ -1557,6 +1663,11 @@ int match_blocks_per_sm(int threads, size_t smem) {
 
 cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int threads, cudaStream_t s) {
     k_build<<<grid, threads, build_smem_bytes(a.bins, a.smem_hits), s>>>(P, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t items = 2 * a.n_events;
+    if (items <= 0) return cudaSuccess;
+    k_order<<<static_cast<unsigned>((items + kOrderThreads - 1) / kOrderThreads), kOrderThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,10 @@ struct BuildArgs {
     int32_t* status;      // [n_events]
     uint8_t* big;         // per-CTA per-hit arrays for larger events
     int64_t big_stride;   // bytes per CTA
+    int32_t* item_class;  // [2 n_events] cost class of each (event, half) seeding item
+    int32_t* class_count; // [128] items per class, zero before the launch
+    int32_t* class_fill;  // [128] places taken per class, zero before the launch
+    int32_t* order;       // [2 n_events] the seeding items, costliest class first
     int32_t* queue;
     unsigned long long* counters;
 };
@@ -58,6 +62,7 @@ struct SeedArgs {
     unsigned long long* pool_ctr;
     int32_t* item_start;
     int32_t* item_count;
+    const int32_t* order;  // the order k_build gave the items
     int32_t* queue;
     unsigned long long* counters;
 };

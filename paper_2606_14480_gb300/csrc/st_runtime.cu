@@ -395,7 +395,7 @@ struct Workspace {
     int32_t cap_max_hits = -1;
     int build_ctas = 0, seed_ctas = 0;  // CTAs the per-CTA scratch is sized for
     // carved pointers
-    int32_t* queues = nullptr;  // [0] build, [1] seed, [2] match
+    int32_t* queues = nullptr;  // [0] build, [1] seed, [2] match; [16, 144) item classes, [144, 272) their fill
     unsigned long long* pool_ctr = nullptr;
     float* cx = nullptr;
     int32_t* corig = nullptr;
@@ -410,6 +410,8 @@ struct Workspace {
     int8_t* pool_n = nullptr;
     int32_t* item_start = nullptr;
     int32_t* item_count = nullptr;
+    int32_t* item_class = nullptr;
+    int32_t* order = nullptr;
 };
 
 struct Pipeline;
@@ -471,6 +473,8 @@ static void tmark(st_ctx* ctx, const Workspace& w, int k, int end, cudaStream_t 
     ctx->tused[k] = true;
 }
 
+// work queues, the pool counter and the item-class counts, zeroed per launch
+constexpr size_t kQueueBytes = 64 + 2 * 128 * sizeof(int32_t);
 constexpr int kBuildSmemHits = 6144;  // larger events keep their per-hit arrays in scratch
 constexpr int kBuildCtasPerSm = 8;
 
@@ -495,7 +499,7 @@ static size_t carve(st_ctx* ctx, Workspace& w, int64_t ne, int64_t nh, int32_t m
     const int build_ctas = ctx->n_sms * kBuildCtasPerSm;
     const int seed_ctas = ctx->n_sms * std::max(1, ctx->seed_bps);
     const int64_t items = 2 * ne;
-    char* q = take(64);
+    char* q = take(kQueueBytes);
     char* cx = take(sizeof(float) * size_t(nh + 3 * ne + 8));
     char* co = take(sizeof(int32_t) * size_t(nh + 3 * ne + 8));
     char* zo = take(sizeof(int32_t) * size_t(ne) * kZoffStride + 4);
@@ -509,6 +513,8 @@ static size_t carve(st_ctx* ctx, Workspace& w, int64_t ne, int64_t nh, int32_t m
     char* pn = take(2 * size_t(sc) + 4);
     char* is = take(sizeof(int32_t) * size_t(items) + 4);
     char* ic = take(sizeof(int32_t) * size_t(items) + 4);
+    char* icl = take(sizeof(int32_t) * size_t(items) + 4);
+    char* ord = take(sizeof(int32_t) * size_t(items) + 4);
     if (base) {
         w.queues = reinterpret_cast<int32_t*>(q);
         w.pool_ctr = reinterpret_cast<unsigned long long*>(q + 32);
@@ -525,6 +531,8 @@ static size_t carve(st_ctx* ctx, Workspace& w, int64_t ne, int64_t nh, int32_t m
         w.pool_n = reinterpret_cast<int8_t*>(pn);
         w.item_start = reinterpret_cast<int32_t*>(is);
         w.item_count = reinterpret_cast<int32_t*>(ic);
+        w.item_class = reinterpret_cast<int32_t*>(icl);
+        w.order = reinterpret_cast<int32_t*>(ord);
         w.cap_events = ne;
         w.cap_hits = nh;
         w.cap_max_hits = mh;
@@ -660,7 +668,7 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
     if (c.ctas_per_sm > 0) sbps = std::min(sbps, c.ctas_per_sm);
     const int g_seed = static_cast<int>(std::max<int64_t>(
         1, std::min<int64_t>({2 * H.n_events, int64_t(ctx->n_sms) * sbps, int64_t(w.seed_ctas)})));
-    ST_CUDA(ctx, cudaMemsetAsync(w.queues, 0, 64, s));
+    ST_CUDA(ctx, cudaMemsetAsync(w.queues, 0, kQueueBytes, s));
     if (H.n_events == 0) {
         ST_CUDA(ctx, cudaMemsetAsync(S.ev_off, 0, sizeof(int32_t), s));
         return ST_OK;
@@ -682,6 +690,10 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
     b.status = S.status;
     b.big = w.big;
     b.big_stride = w.big_stride;
+    b.item_class = w.item_class;
+    b.class_count = w.queues + 16;
+    b.class_fill = w.queues + 16 + 128;
+    b.order = w.order;
     b.queue = w.queues + 0;
     b.counters = ctx->counters;
     tmark(ctx, w, 0, 0, s);
@@ -710,6 +722,7 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
     a.pool_ctr = w.pool_ctr;
     a.item_start = w.item_start;
     a.item_count = w.item_count;
+    a.order = w.order;
     a.queue = w.queues + 1;
     a.counters = ctx->counters;
     tmark(ctx, w, 1, 0, s);

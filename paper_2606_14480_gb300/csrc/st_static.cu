@@ -111,13 +111,15 @@ extern "C" int seeding_run_static(const st_config* cfg, const st_hits* H, st_see
         off += up256(bytes);
         return o;
     };
-    const size_t o_q = take(64);
+    const size_t o_q = take(64 + 2 * 128 * sizeof(int32_t));  // queues, pool counter, item-class counts
     const size_t o_cnt = take(sizeof(unsigned long long) * C_N);
     const size_t o_zoff = take(sizeof(int32_t) * size_t(ne) * kZoffStride + 4);
     const size_t o_cx = take(sizeof(float) * size_t(cont));
     const size_t o_co = take(sizeof(int32_t) * size_t(cont));
     const size_t o_is = take(sizeof(int32_t) * size_t(items) + 4);
     const size_t o_ic = take(sizeof(int32_t) * size_t(items) + 4);
+    const size_t o_icl = take(sizeof(int32_t) * size_t(items) + 4);
+    const size_t o_ord = take(sizeof(int32_t) * size_t(items) + 4);
     const size_t o_ph = take(sizeof(int32_t) * 12 * size_t(S->cap) + 4);
     const size_t o_pp = take(sizeof(float) * 8 * size_t(S->cap) + 4);
     const size_t o_ps = take(sizeof(float) * 4 * size_t(S->cap) + 4);
@@ -173,6 +175,10 @@ extern "C" int seeding_run_static(const st_config* cfg, const st_hits* H, st_see
     ba.status = S->status;
     ba.big = nullptr;
     ba.big_stride = 0;
+    ba.item_class = reinterpret_cast<int32_t*>(b + o_icl);
+    ba.class_count = queues + 16;
+    ba.class_fill = queues + 16 + 128;
+    ba.order = reinterpret_cast<int32_t*>(b + o_ord);
     ba.queue = queues + 0;
     ba.counters = counters;
     e = launch_build(P, ba, g_build, cfg->threads_build, s);
@@ -200,6 +206,7 @@ extern "C" int seeding_run_static(const st_config* cfg, const st_hits* H, st_see
     sa.pool_ctr = pool_ctr;
     sa.item_start = reinterpret_cast<int32_t*>(b + o_is);
     sa.item_count = reinterpret_cast<int32_t*>(b + o_ic);
+    sa.order = ba.order;
     sa.queue = queues + 1;
     sa.counters = counters;
     e = launch_seed(P, sa, g_seed, cfg->threads_seed, s);
