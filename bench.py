@@ -291,7 +291,11 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     graph = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    kernels_per_step = 6  # build, order, seed, scan, gather, match
+    # build, order, seed, scan, gather, and match unless the matching runs
+    # inside the seeding kernel (the HLT1 configuration with CTAs of at most
+    # 256 threads, without final selection or velo_unique)
+    fused = cfg.threads_seed <= 256 and cfg.iter_mode == 0 and not cfg.final_sel and not cfg.velo_unique
+    kernels_per_step = 5 if fused else 6
 
     # ---------------- batched: graph replay, inputs resident in HBM
     with torch.cuda.stream(stream):
@@ -347,10 +351,12 @@ def main():
     units = {k: counters[k] / steps for k in ("pairs", "triplets", "ext_ok", "uv_init", "match_pairs")}
     ops = (OPS_PER_UNIT["pairs"] * units["pairs"] + OPS_PER_UNIT["triplets"] * units["triplets"]
            + OPS_PER_UNIT["fits"] * units["ext_ok"] + OPS_PER_UNIT["uv_init"] * units["uv_init"])
+    if fused:  # the seeding kernel also matches every seed against its event's VELO segments
+        ops += OPS_PER_UNIT["match_pairs"] * units["match_pairs"]
     peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = ops / (seed_ms / 1000.0) / 1e12 if seed_ms > 0 else 0.0
     traffic = traffic_from_profile("k_seed")
-    result["roofline"] = {"kernel": "k_seed", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
+    result["roofline"] = {"kernel": "k_seed (matching fused in)" if fused else "k_seed", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
                           "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                           "peak_source": f"FP32: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                                          f"({src} sm_max_mhz)",
@@ -358,8 +364,11 @@ def main():
                           "units_per_launch": units,
                           "hbm": {"algorithmic_bytes": None, "peak_gbs": float(peaks.get("hbm_gbs", 6800.0))}}
     # algorithmic HBM bytes of one seeding launch: containers (x, original
-    # index) read once, seed records (48 + 32 + 16 + 2 B) written once
+    # index) read once, seed records (48 + 32 + 16 + 2 B) written once; fused,
+    # also the VELO states (16 B) read once and a (VELO index, chi2) per seed
     alg_bytes = 8.0 * batch.n_hits + 98.0 * counters["seeds"] / steps
+    if fused:
+        alg_bytes += 16.0 * batch.velo.shape[0] + 8.0 * counters["seeds"] / steps
     result["roofline"]["hbm"]["algorithmic_bytes"] = alg_bytes
     result["roofline"]["hbm"]["achieved_gbs"] = alg_bytes / (seed_ms / 1000.0) / 1e9 if seed_ms > 0 else 0.0
     # instruction-issue view of the same launch: warp instructions (ncu, same
@@ -467,7 +476,7 @@ def main():
         pe_ms = marks[0].elapsed_time(marks[-1])
         per = np.array([a.elapsed_time(b) for a, b in zip(marks, marks[1:])])
         result["per_event"] = {"value": pe / (pe_ms / 1000.0), "unit": "events/s", "events_timed": pe,
-                               "launches_per_event": kernels_per_step,
+                               "launches_per_event": 6,
                                "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
                                "mode": "seeding_run + matching_run per event, one stream (latency: between "
                                        "consecutive events' completion on the stream)"}

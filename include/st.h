@@ -301,7 +301,13 @@ int st_set_ghost_nn(st_ctx* ctx, const float* weights, int32_t n);
 /* Capture seeding_run + matching_run for these exact buffers and sizes into a
  * CUDA graph (persistent, work-queue kernels).  Scratch must be reserved
  * first (st_reserve).  The arguments' pointers must stay valid while the
- * graph exists.  *out receives the graph; launch with st_graph_launch. */
+ * graph exists.  *out receives the graph; launch with st_graph_launch.
+ * With threads_seed <= 256, iter_mode 0 and no final selection the matching
+ * runs inside the seeding kernel (each event as soon as its two halves are
+ * seeded); the outputs are those of the two calls.  If that kernel ever gave
+ * up a (bounded) wait for an event being seeded, which a correct run cannot
+ * do, every event of the launch gets status ST_TIMEOUT.  The serving pipeline
+ * runs batches the same way. */
 int st_graph_create(st_ctx* ctx, const st_hits* hits, const st_velo* velo, st_seeds* seeds,
                     st_long* out, st_graph** graph);
 int st_graph_launch(st_graph* graph, void* cuda_stream);

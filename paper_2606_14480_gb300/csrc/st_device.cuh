@@ -248,4 +248,10 @@ __device__ __forceinline__ int warp_sum(int v) {
     return v;
 }
 
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 }  // namespace st

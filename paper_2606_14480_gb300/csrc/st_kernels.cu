@@ -13,7 +13,9 @@
 //             compensated least-squares fit, O(n) clone killing with a 64-bit
 //             atomicMin table, UV seeding (iterative or Hough clusters) with a
 //             64-bit atomicMin per seed, and the seed records; HLT2-style
-//             iterations run as passes with a taken-hit bitmask.
+//             iterations run as passes with a taken-hit bitmask.  In the
+//             batch path the CTA that finishes an event's second half also
+//             matches the event.
 //   k_scan / k_gather   per-event CSR of the seed records.
 //   k_match   one event per item: VELO segments bucketed by ty in shared
 //             memory, one thread per seed for its lowest chi2_match, then
@@ -659,9 +661,36 @@ size_t seed_slot_bytes(int cand_cap, int max_xhits) {
 // two per SM (64 registers).
 constexpr int kSeedBlocks256 = 5;
 
+// Matching of one event, shared by k_match and the fused seeding kernel
+// (defined with the matching kernel below).
+struct MatchIO {
+    const float* velo;         // x, y, tx, ty at z_velo
+    const float* seed_state;   // x, y, tx, ty at z_state, per row
+    const int8_t* seed_n;      // (nx, nuv) per row
+    int32_t* velo_idx;         // per row
+    float* chi2;               // per row
+    float* ghost_prob;         // per row (final selection)
+};
+template <bool kFinal, class Row>
+__device__ int match_event(const DevParams& P, const MatchIO& M, int VS, unsigned char* msm, int64_t v0, int nv,
+                           int ns, Row row, int* s_cnt, ull& n_grid, ull& n_presel);
+
+constexpr int kDeferRounds = 2;       // matching left to idle CTAs once fewer seeding items than this per CTA remain
+constexpr int kReadySpins = 1 << 22;  // polls (100 ns apart) of an announcement before giving up
+
 // kSeq: compiled with the HLT2-style pass loop and taken-hit checks; the HLT1
 // instantiation has neither (they fold away).
-template <int kT, int kB, bool kSeq>
+// kFuse: the kernel also matches each event, where the pool holds its
+// records (HLT1 instantiation only).  The CTA that finishes the second of an
+// event's two halves (a per-event counter) matches the event before its next
+// item.  With defer_match, once fewer than kDeferRounds seeding items per CTA
+// are left it announces the event in a ready list instead, and CTAs that find
+// no seeding item left take the announced events (short items at the end
+// balance the CTAs' finishing times); such a CTA waits (bounded) only while
+// some event is still being seeded by a running CTA.  Kernels that share the
+// GPU with others (the serving pipeline) do not defer: a waiting CTA would
+// hold resources the other kernels could use.
+template <int kT, int kB, bool kSeq, bool kFuse>
 __global__ void __launch_bounds__(kT, kB)
 k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -716,22 +745,102 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     uint32_t* g_used = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(hn + CC) + 3) & ~uintptr_t(3));
     constexpr bool seq = kSeq;
     const uint32_t* used = kSeq ? g_used : nullptr;
-    __shared__ int s_nvalid;
+    __shared__ int s_nvalid, s_cnt, s_match;
+    __shared__ ull s_mctr[3];
+    if (kFuse && tid < 3) s_mctr[tid] = 0;
     int spar = 0;  // which half of tmp the next block scan uses
 
     ull ctr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
+    int64_t fin = -1;  // fused: event of the half this CTA finished last
     for (;;) {
+        if (kFuse && fin >= 0) __threadfence();  // the half's records, before its count
         __syncthreads();
         if (tid == 0) {
-            const int q = atomicAdd(A.queue, 1);
-            s_item = q < 2 * A.n_events ? A.order[q] : q;
+            s_match = -1;
+            const int n2 = static_cast<int>(2 * A.n_events);
+            if (kFuse && fin >= 0 && atomicAdd(A.ev_done + fin, 1) == 1) {
+                // this CTA finished the event's second half (the other half's
+                // records were released before its count; the fence orders
+                // them before the reads of the matching)
+                __threadfence();
+                const int left = n2 - min(*reinterpret_cast<volatile int*>(A.queue), n2);
+                if (!A.defer_match || left >= kDeferRounds * static_cast<int>(gridDim.x)) {
+                    s_match = static_cast<int>(fin);  // matched by this CTA, now
+                } else {
+                    // near the end: left for whichever CTA runs out of seeding items first
+                    atomicExch(A.ready + atomicAdd(A.ready_ctr, 1), static_cast<int>(fin) + 1);
+                    __threadfence();
+                }
+                atomicAdd(A.done_ctr, 1);
+            }
+            if (s_match < 0) {
+                const int q = atomicAdd(A.queue, 1);
+                if (q < n2) {
+                    s_item = A.order[q];
+                } else if (kFuse && A.defer_match) {
+                    // no seeding item left, and each is held by a running CTA:
+                    // take the next announced event, or stop once every event
+                    // is done and none is left for this slot
+                    const int n = static_cast<int>(A.n_events);
+                    const int m = atomicAdd(A.m_claim, 1);
+                    const volatile int* vr = A.ready;
+                    int v = 0;
+                    bool gave_up = true;
+                    for (int it = 0; it < kReadySpins; ++it) {
+                        if (m < n) v = vr[m];
+                        if (v) {
+                            gave_up = false;
+                            break;
+                        }
+                        if (*reinterpret_cast<volatile int*>(A.done_ctr) >= n) {
+                            __threadfence();
+                            if (m < n) v = vr[m];
+                            gave_up = false;
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                    if (gave_up) atomicExch(A.fault, 1);
+                    __threadfence();
+                    s_match = v - 1;
+                    s_item = -1;
+                } else {
+                    s_item = -1;
+                }
+            }
         }
         __syncthreads();
+        fin = -1;
+        if (kFuse && s_match >= 0) {
+            const int64_t em = s_match;
+            const int c0 = __ldcg(A.item_count + 2 * em), c1 = __ldcg(A.item_count + 2 * em + 1);
+            const int64_t r0 = c0 ? __ldcg(A.item_start + 2 * em) : 0;
+            const int64_t r1 = c1 ? __ldcg(A.item_start + 2 * em + 1) : 0;
+            const int64_t v0 = A.velo_off[em];
+            const MatchIO M{A.velo, A.pool_state, A.pool_n, A.pool_velo, A.pool_chi2, nullptr};
+            ull ng = 0, np = 0;
+            const int nl = match_event<false>(P, M, A.velo_smem, smem, v0,
+                                                    static_cast<int>(A.velo_off[em + 1] - v0), c0 + c1,
+                                                    [&](int s) { return s < c0 ? r0 + s : r1 + (s - c0); },
+                                                    &s_cnt, ng, np);
+            ng = warp_sum(ng);
+            np = warp_sum(np);
+            if ((tid & 31) == 0) {
+                atomicAdd(&s_mctr[0], ng);
+                atomicAdd(&s_mctr[1], np);
+            }
+            if (tid == 0) {
+                atomicAdd(&s_mctr[2], ull(nl));
+                if (A.n_long) A.n_long[em] = nl;
+            }
+            continue;
+        }
         const int64_t item = s_item;
-        if (item >= 2 * A.n_events) break;
+        if (item < 0) break;
         const int64_t e = item >> 1;
         const int h = static_cast<int>(item & 1);
+        if (kFuse) fin = e;
         if (A.status[e] != 0) {
             if (tid == 0) A.item_count[item] = 0;
             continue;
@@ -1219,6 +1328,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
         }
     }
     flush_counters(A.counters + C_PAIRS, ctr, 8);
+    if (kFuse && tid < 3 && s_mctr[tid]) atomicAdd(A.counters + C_MATCH_PAIRS + tid, s_mctr[tid]);
 }
 
 // ===========================================================================
@@ -1245,13 +1355,21 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ GatherArg
 // output arrays allow it).
 template <bool kVec>
 __global__ void __launch_bounds__(256) k_gather(const __grid_constant__ GatherArgs A) {
+    const bool fault = A.fault && *A.fault;
     for (int64_t e = blockIdx.x; e < A.n_events; e += gridDim.x) {
+        if (fault && threadIdx.x == 0) A.status[e] = -4;  // ST_TIMEOUT: the fused matching gave up a wait
         const int c0 = A.item_count[2 * e], c1 = A.item_count[2 * e + 1];
         const int n = c0 + c1;
         if (n == 0) continue;
         const int64_t s0 = A.item_start[2 * e], s1 = A.item_start[2 * e + 1];
         const int64_t d0 = A.ev_off[e];
         auto src = [&](int k) { return k < c0 ? s0 + k : s1 + (k - c0); };
+        if (A.pool_velo) {
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                A.velo_idx[d0 + k] = A.pool_velo[src(k)];
+                A.chi2[d0 + k] = A.pool_chi2[src(k)];
+            }
+        }
         if (kVec) {
             const uint4* ph = reinterpret_cast<const uint4*>(A.pool_hits);
             const uint4* pp = reinterpret_cast<const uint4*>(A.pool_params);
@@ -1379,19 +1497,20 @@ __device__ float ghost_nn(const DevParams& P, const float f[8]) {
     return 1.f / (1.f + expf(-z));
 }
 
-// One event per work item; one thread per seed.  The event's VELO segments
-// are staged in shared memory with their float-float extrapolations and
-// bucketed by ty, so a seed only visits the buckets its |dty| cut can reach
-// (every other pair fails that cut).  Events with more segments than fit are
-// processed in chunks, each scanned in full.
-// kFinal: compiled with the final selection of Section 4.4 (the plain
-// instantiation does not carry its registers).
-template <bool kFinal>
-__global__ void __launch_bounds__(kMaxThreads)
-k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int VS = A.velo_smem, T = blockDim.x, tid = threadIdx.x;
-    float* vxh = reinterpret_cast<float*>(smem);
+// Matching of one event (Section 4), one thread per seed: the event's VELO
+// segments are staged in shared memory (msm, match_smem_bytes(VS) bytes) with
+// their float-float extrapolations and bucketed by ty, so a seed only visits
+// the buckets its |dty| cut can reach (every other pair fails that cut).
+// Events with more segments than fit are processed in chunks, each scanned in
+// full.  Seed s (0 .. ns-1, in the event's canonical seed order) reads its
+// state and hit counts and writes its pair at index row(s) of M's arrays.
+// Returns the event's Long-track count; n_grid / n_presel accumulate this
+// thread's pair counts.
+template <bool kFinal, class Row>
+__device__ int match_event(const DevParams& P, const MatchIO& M, int VS, unsigned char* msm, int64_t v0, int nv,
+                           int ns, Row row, int* s_cnt, ull& n_grid, ull& n_presel) {
+    const int T = blockDim.x, tid = threadIdx.x;
+    float* vxh = reinterpret_cast<float*>(msm);
     float* vxl = vxh + VS;
     float* vyh = vxl + VS;
     float* vyl = vyh + VS;
@@ -1403,15 +1522,218 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
     int* boff = bcnt + kTyBins;                    // [kTyBins + 1]
     unsigned* vmin = reinterpret_cast<unsigned*>(boff + kTyBins + 8);  // final selection: lowest ghost
                                                                        // probability per VELO segment
+    if (tid == 0) *s_cnt = 0;
+    const bool bucketed = nv <= VS;
+    for (int vc = 0; vc < nv; vc += VS) {
+        const int m = min(VS, nv - vc);
+        for (int k = tid; k < kTyBins; k += T) bcnt[k] = 0;
+        __syncthreads();
+        for (int v = tid; v < m; v += T) {
+            const float* st = M.velo + (v0 + vc + v) * 4;
+            const float x = st[0], y = st[1], tx = st[2], ty = st[3];
+            float p, pe, s, se;
+            two_prod(P.dAV_hi, tx, p, pe);
+            two_sum(x, p, s, se);
+            vxh[v] = s;
+            vxl[v] = se + fmaf(P.dAV_lo, tx, pe);
+            two_prod(P.dMV_hi, ty, p, pe);
+            two_sum(y, p, s, se);
+            vyh[v] = s;
+            vyl[v] = se + fmaf(P.dMV_lo, ty, pe);
+            vtx[v] = tx;
+            vty[v] = ty;
+            vit[v] = 1.f / fmaf(P.toly_b, fmaf(tx, tx, ty * ty), P.toly_a);
+            if (bucketed) atomicAdd(&bcnt[ty_bin(ty)], 1);
+        }
+        __syncthreads();
+        if (bucketed) {
+            if (tid < 32) {  // exclusive scan of the bucket counts by one warp
+                int c0 = bcnt[2 * tid], c1 = bcnt[2 * tid + 1];
+                int x = c0 + c1;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (tid >= o) x += y;
+                }
+                const int ex = x - c0 - c1;
+                boff[2 * tid] = ex;
+                boff[2 * tid + 1] = ex + c0;
+                if (tid == 31) boff[kTyBins] = x;
+            }
+            __syncthreads();
+            for (int q = tid; q < kTyBins; q += T) bcnt[q] = boff[q];  // reuse as fill cursors
+            __syncthreads();
+            for (int v = tid; v < m; v += T) bidx[atomicAdd(&bcnt[ty_bin(vty[v])], 1)] = v;
+            __syncthreads();
+        }
+        for (int s = tid; s < ns; s += T) {
+            // read past L1: in the fused kernel other CTAs wrote the rows during this launch
+            const float* st = M.seed_state + row(s) * 4;
+            const float xS = __ldcg(st), yS = __ldcg(st + 1), txS = __ldcg(st + 2), tyS = __ldcg(st + 3);
+            float p, pe, xh, xl, yh, yl;
+            two_prod(P.dAS_hi, txS, p, pe);
+            two_sum(xS, p, xh, xl);
+            xl += fmaf(P.dAS_lo, txS, pe);
+            two_prod(P.dMS_hi, tyS, p, pe);
+            two_sum(yS, p, yh, yl);
+            yl += fmaf(P.dMS_lo, tyS, pe);
+            const float dzx = P.Dx * fabsf(xS);
+            float best = FLT_MAX;
+            int bv = 0x7fffffff;
+            if (vc > 0) {
+                const int pv = M.velo_idx[row(s)];
+                if (pv >= 0) {
+                    bv = pv;
+                    best = M.chi2[row(s)];
+                }
+            }
+            int npre = 0;
+            if (bucketed) {
+                // buckets that can hold |ty - tyS| < cut_ty (slightly widened;
+                // the exact cut is applied per pair)
+                const float w = P.cut_ty + 1e-6f * (fabsf(tyS) + P.cut_ty);
+                const int k0 = boff[ty_bin(tyS - w)], k1 = boff[ty_bin(tyS + w) + 1];
+                for (int k = k0; k < k1; ++k) {
+                    const int v = bidx[k];
+                    npre += match_pair(P, vxh[v], vxl[v], vyh[v], vyl[v], vtx[v], vty[v], vit[v], vc + v,
+                                       xh, xl, yh, yl, txS, tyS, dzx, best, bv);
+                }
+            } else {
+                for (int v = 0; v < m; ++v)
+                    npre += match_pair(P, vxh[v], vxl[v], vyh[v], vyl[v], vtx[v], vty[v], vit[v], vc + v,
+                                       xh, xl, yh, yl, txS, tyS, dzx, best, bv);
+            }
+            n_presel += npre;
+            n_grid += m;
+            const bool found = best < FLT_MAX;
+            M.velo_idx[row(s)] = found ? bv : -1;
+            M.chi2[row(s)] = found ? best : 0.f;
+        }
+        __syncthreads();
+    }
+    if (nv == 0) {
+        for (int s = tid; s < ns; s += T) {
+            M.velo_idx[row(s)] = -1;
+            M.chi2[row(s)] = 0.f;
+        }
+    }
+    __syncthreads();
+    if (P.velo_unique) {
+        // a VELO segment keeps its best seed (lowest chi2, then lower seed
+        // index); losers are marked -2 - v so that concurrent readers still
+        // see which segment they held
+        for (int s = tid; s < ns; s += T) {
+            const int v = M.velo_idx[row(s)];
+            if (v < 0) continue;
+            const float c = M.chi2[row(s)];
+            for (int t = 0; t < ns; ++t) {
+                if (t == s) continue;
+                int vt = M.velo_idx[row(t)];
+                if (vt <= -2) vt = -2 - vt;
+                if (vt != v) continue;
+                const float ct = M.chi2[row(t)];
+                if (ct < c || (ct == c && t < s)) {
+                    M.velo_idx[row(s)] = -2 - v;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        for (int s = tid; s < ns; s += T) {
+            if (M.velo_idx[row(s)] <= -2) {
+                M.velo_idx[row(s)] = -1;
+                M.chi2[row(s)] = 0.f;
+            }
+        }
+        __syncthreads();
+    }
+    if (kFinal && P.final_sel) {
+        // Section 4.4: ghost probability of each best pair and the cut
+        for (int s = tid; s < ns; s += T) {
+            const int v = M.velo_idx[row(s)];
+            float p = 1.f;
+            if (v >= 0) {
+                float f[8];
+                pair_features(P, M.velo + (v0 + v) * 4, M.seed_state + row(s) * 4, f);
+                f[5] = M.chi2[row(s)];
+                f[7] = static_cast<float>(M.seed_n[2 * row(s)] + M.seed_n[2 * row(s) + 1]);
+                p = ghost_nn(P, f);
+                if (!(p < P.ghost_max)) {
+                    M.velo_idx[row(s)] = -1;
+                    M.chi2[row(s)] = 0.f;
+                }
+            }
+            M.ghost_prob[row(s)] = p;
+        }
+        __syncthreads();
+        // clones: a kept pair whose VELO segment another kept pair holds
+        // with a ghost probability lower by at least clone_margin (one
+        // pair per seed, so no two pairs share a seed); marked -2 - v.
+        // With clone_margin > 0 that is p - (lowest p on the segment) >=
+        // clone_margin; the lowest p per segment is an atomicMin of the
+        // probabilities' bits (non-negative floats order as unsigned).
+        if (nv <= VS) {
+            for (int v = tid; v < nv; v += T) vmin[v] = 0x7f800000u;
+            __syncthreads();
+            for (int s = tid; s < ns; s += T) {
+                const int v = M.velo_idx[row(s)];
+                if (v >= 0) atomicMin(&vmin[v], __float_as_uint(M.ghost_prob[row(s)]));
+            }
+            __syncthreads();
+            for (int s = tid; s < ns; s += T) {
+                const int v = M.velo_idx[row(s)];
+                if (v >= 0 && M.ghost_prob[row(s)] - __uint_as_float(vmin[v]) >= P.clone_margin)
+                    M.velo_idx[row(s)] = -2 - v;
+            }
+        } else {
+            for (int s = tid; s < ns; s += T) {
+                const int v = M.velo_idx[row(s)];
+                if (v < 0) continue;
+                const float p = M.ghost_prob[row(s)];
+                for (int t = 0; t < ns; ++t) {
+                    if (t == s) continue;
+                    int vt = M.velo_idx[row(t)];
+                    if (vt <= -2) vt = -2 - vt;
+                    if (vt == v && p - M.ghost_prob[row(t)] >= P.clone_margin) {
+                        M.velo_idx[row(s)] = -2 - v;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int s = tid; s < ns; s += T) {
+            if (M.velo_idx[row(s)] <= -2) {
+                M.velo_idx[row(s)] = -1;
+                M.chi2[row(s)] = 0.f;
+            }
+        }
+        __syncthreads();
+    }
+    int nl = 0;
+    for (int s = tid; s < ns; s += T) nl += M.velo_idx[row(s)] >= 0;
+    nl = warp_sum(nl);
+    if ((tid & 31) == 0 && nl) atomicAdd(s_cnt, nl);
+    __syncthreads();
+    return *s_cnt;
+}
+
+// One event per work item (match_event), for matching_run on seeds in the
+// per-event CSR layout.
+// kFinal: compiled with the final selection of Section 4.4 (the plain
+// instantiation does not carry its registers).
+template <bool kFinal>
+__global__ void __launch_bounds__(kMaxThreads)
+k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x;
     __shared__ int s_item, s_cnt;
     ull ctr[3] = {0, 0, 0};
+    const MatchIO M{A.velo, A.seed_state, A.seed_n, A.velo_idx, A.chi2, A.ghost_prob};
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) {
-            s_item = atomicAdd(A.queue, 1);
-            s_cnt = 0;
-        }
+        if (tid == 0) s_item = atomicAdd(A.queue, 1);
         __syncthreads();
         const int64_t e = s_item;
         if (e >= A.n_events) break;
@@ -1419,200 +1741,11 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
         const int nv = static_cast<int>(A.velo_off[e + 1] - v0);
         const int64_t s0 = A.seed_off[e];
         const int ns = A.seed_off[e + 1] - static_cast<int>(s0);
-        const bool bucketed = nv <= VS;
-        for (int vc = 0; vc < nv; vc += VS) {
-            const int m = min(VS, nv - vc);
-            for (int k = tid; k < kTyBins; k += T) bcnt[k] = 0;
-            __syncthreads();
-            for (int v = tid; v < m; v += T) {
-                const float* st = A.velo + (v0 + vc + v) * 4;
-                const float x = st[0], y = st[1], tx = st[2], ty = st[3];
-                float p, pe, s, se;
-                two_prod(P.dAV_hi, tx, p, pe);
-                two_sum(x, p, s, se);
-                vxh[v] = s;
-                vxl[v] = se + fmaf(P.dAV_lo, tx, pe);
-                two_prod(P.dMV_hi, ty, p, pe);
-                two_sum(y, p, s, se);
-                vyh[v] = s;
-                vyl[v] = se + fmaf(P.dMV_lo, ty, pe);
-                vtx[v] = tx;
-                vty[v] = ty;
-                vit[v] = 1.f / fmaf(P.toly_b, fmaf(tx, tx, ty * ty), P.toly_a);
-                if (bucketed) atomicAdd(&bcnt[ty_bin(ty)], 1);
-            }
-            __syncthreads();
-            if (bucketed) {
-                if (tid < 32) {  // exclusive scan of the bucket counts by one warp
-                    int c0 = bcnt[2 * tid], c1 = bcnt[2 * tid + 1];
-                    int x = c0 + c1;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, x, o);
-                        if (tid >= o) x += y;
-                    }
-                    const int ex = x - c0 - c1;
-                    boff[2 * tid] = ex;
-                    boff[2 * tid + 1] = ex + c0;
-                    if (tid == 31) boff[kTyBins] = x;
-                }
-                __syncthreads();
-                for (int q = tid; q < kTyBins; q += T) bcnt[q] = boff[q];  // reuse as fill cursors
-                __syncthreads();
-                for (int v = tid; v < m; v += T) bidx[atomicAdd(&bcnt[ty_bin(vty[v])], 1)] = v;
-                __syncthreads();
-            }
-            for (int s = tid; s < ns; s += T) {
-                const float* st = A.seed_state + (s0 + s) * 4;
-                const float xS = st[0], yS = st[1], txS = st[2], tyS = st[3];
-                float p, pe, xh, xl, yh, yl;
-                two_prod(P.dAS_hi, txS, p, pe);
-                two_sum(xS, p, xh, xl);
-                xl += fmaf(P.dAS_lo, txS, pe);
-                two_prod(P.dMS_hi, tyS, p, pe);
-                two_sum(yS, p, yh, yl);
-                yl += fmaf(P.dMS_lo, tyS, pe);
-                const float dzx = P.Dx * fabsf(xS);
-                float best = FLT_MAX;
-                int bv = 0x7fffffff;
-                if (vc > 0) {
-                    const int pv = A.velo_idx[s0 + s];
-                    if (pv >= 0) {
-                        bv = pv;
-                        best = A.chi2[s0 + s];
-                    }
-                }
-                int npre = 0;
-                if (bucketed) {
-                    // buckets that can hold |ty - tyS| < cut_ty (slightly widened;
-                    // the exact cut is applied per pair)
-                    const float w = P.cut_ty + 1e-6f * (fabsf(tyS) + P.cut_ty);
-                    const int k0 = boff[ty_bin(tyS - w)], k1 = boff[ty_bin(tyS + w) + 1];
-                    for (int k = k0; k < k1; ++k) {
-                        const int v = bidx[k];
-                        npre += match_pair(P, vxh[v], vxl[v], vyh[v], vyl[v], vtx[v], vty[v], vit[v], vc + v,
-                                           xh, xl, yh, yl, txS, tyS, dzx, best, bv);
-                    }
-                } else {
-                    for (int v = 0; v < m; ++v)
-                        npre += match_pair(P, vxh[v], vxl[v], vyh[v], vyl[v], vtx[v], vty[v], vit[v], vc + v,
-                                           xh, xl, yh, yl, txS, tyS, dzx, best, bv);
-                }
-                ctr[1] += npre;
-                ctr[0] += m;
-                const bool found = best < FLT_MAX;
-                A.velo_idx[s0 + s] = found ? bv : -1;
-                A.chi2[s0 + s] = found ? best : 0.f;
-            }
-            __syncthreads();
-        }
-        if (nv == 0) {
-            for (int s = tid; s < ns; s += T) {
-                A.velo_idx[s0 + s] = -1;
-                A.chi2[s0 + s] = 0.f;
-            }
-        }
-        __syncthreads();
-        if (P.velo_unique) {
-            // a VELO segment keeps its best seed (lowest chi2, then lower seed
-            // index); losers are marked -2 - v so that concurrent readers still
-            // see which segment they held
-            for (int s = tid; s < ns; s += T) {
-                const int v = A.velo_idx[s0 + s];
-                if (v < 0) continue;
-                const float c = A.chi2[s0 + s];
-                for (int t = 0; t < ns; ++t) {
-                    if (t == s) continue;
-                    int vt = A.velo_idx[s0 + t];
-                    if (vt <= -2) vt = -2 - vt;
-                    if (vt != v) continue;
-                    const float ct = A.chi2[s0 + t];
-                    if (ct < c || (ct == c && t < s)) {
-                        A.velo_idx[s0 + s] = -2 - v;
-                        break;
-                    }
-                }
-            }
-            __syncthreads();
-            for (int s = tid; s < ns; s += T) {
-                if (A.velo_idx[s0 + s] <= -2) {
-                    A.velo_idx[s0 + s] = -1;
-                    A.chi2[s0 + s] = 0.f;
-                }
-            }
-            __syncthreads();
-        }
-        if (kFinal && P.final_sel) {
-            // Section 4.4: ghost probability of each best pair and the cut
-            for (int s = tid; s < ns; s += T) {
-                const int v = A.velo_idx[s0 + s];
-                float p = 1.f;
-                if (v >= 0) {
-                    float f[8];
-                    pair_features(P, A.velo + (v0 + v) * 4, A.seed_state + (s0 + s) * 4, f);
-                    f[5] = A.chi2[s0 + s];
-                    f[7] = static_cast<float>(A.seed_n[2 * (s0 + s)] + A.seed_n[2 * (s0 + s) + 1]);
-                    p = ghost_nn(P, f);
-                    if (!(p < P.ghost_max)) {
-                        A.velo_idx[s0 + s] = -1;
-                        A.chi2[s0 + s] = 0.f;
-                    }
-                }
-                A.ghost_prob[s0 + s] = p;
-            }
-            __syncthreads();
-            // clones: a kept pair whose VELO segment another kept pair holds
-            // with a ghost probability lower by at least clone_margin (one
-            // pair per seed, so no two pairs share a seed); marked -2 - v.
-            // With clone_margin > 0 that is p - (lowest p on the segment) >=
-            // clone_margin; the lowest p per segment is an atomicMin of the
-            // probabilities' bits (non-negative floats order as unsigned).
-            if (nv <= VS) {
-                for (int v = tid; v < nv; v += T) vmin[v] = 0x7f800000u;
-                __syncthreads();
-                for (int s = tid; s < ns; s += T) {
-                    const int v = A.velo_idx[s0 + s];
-                    if (v >= 0) atomicMin(&vmin[v], __float_as_uint(A.ghost_prob[s0 + s]));
-                }
-                __syncthreads();
-                for (int s = tid; s < ns; s += T) {
-                    const int v = A.velo_idx[s0 + s];
-                    if (v >= 0 && A.ghost_prob[s0 + s] - __uint_as_float(vmin[v]) >= P.clone_margin)
-                        A.velo_idx[s0 + s] = -2 - v;
-                }
-            } else {
-                for (int s = tid; s < ns; s += T) {
-                    const int v = A.velo_idx[s0 + s];
-                    if (v < 0) continue;
-                    const float p = A.ghost_prob[s0 + s];
-                    for (int t = 0; t < ns; ++t) {
-                        if (t == s) continue;
-                        int vt = A.velo_idx[s0 + t];
-                        if (vt <= -2) vt = -2 - vt;
-                        if (vt == v && p - A.ghost_prob[s0 + t] >= P.clone_margin) {
-                            A.velo_idx[s0 + s] = -2 - v;
-                            break;
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            for (int s = tid; s < ns; s += T) {
-                if (A.velo_idx[s0 + s] <= -2) {
-                    A.velo_idx[s0 + s] = -1;
-                    A.chi2[s0 + s] = 0.f;
-                }
-            }
-            __syncthreads();
-        }
-        int nl = 0;
-        for (int s = tid; s < ns; s += T) nl += A.velo_idx[s0 + s] >= 0;
-        nl = warp_sum(nl);
-        if ((tid & 31) == 0 && nl) atomicAdd(&s_cnt, nl);
-        __syncthreads();
+        const int nl = match_event<kFinal>(P, M, A.velo_smem, smem, v0, nv, ns,
+                                           [&](int s) { return s0 + s; }, &s_cnt, ctr[0], ctr[1]);
         if (tid == 0) {
-            if (A.n_long) A.n_long[e] = s_cnt;
-            ctr[2] += s_cnt;
+            if (A.n_long) A.n_long[e] = nl;
+            ctr[2] += nl;
         }
     }
     flush_counters(A.counters + C_MATCH_PAIRS, ctr, 3);
@@ -1626,10 +1759,11 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
 // next to the kernel's own static shared memory (opt-in maximum - static).
 cudaError_t set_smem_limits(size_t optin) {
     const void* fns[] = {reinterpret_cast<const void*>(k_build),
-                         reinterpret_cast<const void*>(k_seed<256, kSeedBlocks256, false>),
-                         reinterpret_cast<const void*>(k_seed<kMaxThreads, 2, false>),
-                         reinterpret_cast<const void*>(k_seed<256, kSeedBlocks256, true>),
-                         reinterpret_cast<const void*>(k_seed<kMaxThreads, 2, true>),
+                         reinterpret_cast<const void*>(k_seed<256, kSeedBlocks256, false, false>),
+                         reinterpret_cast<const void*>(k_seed<kMaxThreads, 2, false, false>),
+                         reinterpret_cast<const void*>(k_seed<256, kSeedBlocks256, true, false>),
+                         reinterpret_cast<const void*>(k_seed<kMaxThreads, 2, true, false>),
+                         reinterpret_cast<const void*>(k_seed<256, kSeedBlocks256, false, true>),
                          reinterpret_cast<const void*>(k_match<false>), reinterpret_cast<const void*>(k_match<true>)};
     for (const void* f : fns) {
         cudaFuncAttributes fa;
@@ -1650,9 +1784,9 @@ int build_blocks_per_sm(int threads, size_t smem) {
 int seed_blocks_per_sm(int threads, size_t smem) {
     int n = 0;
     if (threads <= 256)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed<256, kSeedBlocks256, false>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed<256, kSeedBlocks256, false, false>, threads, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed<kMaxThreads, 2, false>, threads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_seed<kMaxThreads, 2, false, false>, threads, smem);
     return n;
 }
 int match_blocks_per_sm(int threads, size_t smem) {
@@ -1674,12 +1808,15 @@ cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int t
 cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s) {
     const size_t smem = seed_smem_bytes(threads, a.smem_hits, a.tbl_smem, a.key_smem);
     const bool sq = P.iter_mode == 1;
-    if (threads <= 256) {
-        if (sq) k_seed<256, kSeedBlocks256, true><<<grid, threads, smem, s>>>(P, a);
-        else k_seed<256, kSeedBlocks256, false><<<grid, threads, smem, s>>>(P, a);
+    if (a.velo) {  // fused matching: the runtime only asks for it where this instantiation applies
+        if (threads > 256 || sq) return cudaErrorInvalidValue;
+        k_seed<256, kSeedBlocks256, false, true><<<grid, threads, smem, s>>>(P, a);
+    } else if (threads <= 256) {
+        if (sq) k_seed<256, kSeedBlocks256, true, false><<<grid, threads, smem, s>>>(P, a);
+        else k_seed<256, kSeedBlocks256, false, false><<<grid, threads, smem, s>>>(P, a);
     } else {
-        if (sq) k_seed<kMaxThreads, 2, true><<<grid, threads, smem, s>>>(P, a);
-        else k_seed<kMaxThreads, 2, false><<<grid, threads, smem, s>>>(P, a);
+        if (sq) k_seed<kMaxThreads, 2, true, false><<<grid, threads, smem, s>>>(P, a);
+        else k_seed<kMaxThreads, 2, false, false><<<grid, threads, smem, s>>>(P, a);
     }
     return cudaGetLastError();
 }

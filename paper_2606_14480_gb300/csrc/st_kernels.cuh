@@ -65,6 +65,22 @@ struct SeedArgs {
     const int32_t* order;  // the order k_build gave the items
     int32_t* queue;
     unsigned long long* counters;
+    // matching fused into the seeding kernel (velo null: seeding only): the
+    // CTA that finishes an event's second half matches the event, or near
+    // the end announces it for CTAs without seeding work
+    const int64_t* velo_off = nullptr;
+    const float* velo = nullptr;
+    int32_t velo_smem = 0;
+    int32_t defer_match = 0;       // near the end, leave matching to CTAs without seeding work
+    int32_t* ev_done = nullptr;    // [n_events] halves finished; zero before the launch
+    int32_t* ready = nullptr;      // [n_events] announced events (event + 1); zero before
+    int32_t* ready_ctr = nullptr;  // events announced; zero before
+    int32_t* m_claim = nullptr;    // announcements claimed; zero before
+    int32_t* done_ctr = nullptr;   // events with both halves finished; zero before
+    int32_t* fault = nullptr;      // set if a wait gave up; zero before
+    int32_t* pool_velo = nullptr;  // [pool_cap] matched VELO segment per seed record
+    float* pool_chi2 = nullptr;    // [pool_cap]
+    int32_t* n_long = nullptr;     // [n_events], may be null
 };
 
 struct GatherArgs {
@@ -82,6 +98,12 @@ struct GatherArgs {
     float* state;
     int8_t* n_hits;
     int32_t* status;
+    // fused matching: its per-record results go to the Long-track arrays too
+    const int32_t* pool_velo = nullptr;  // null: nothing to copy
+    const float* pool_chi2 = nullptr;
+    int32_t* velo_idx = nullptr;
+    float* chi2 = nullptr;
+    const int32_t* fault = nullptr;      // non-zero: every event of the launch gets ST_TIMEOUT
 };
 
 struct MatchArgs {

@@ -395,7 +395,9 @@ struct Workspace {
     int32_t cap_max_hits = -1;
     int build_ctas = 0, seed_ctas = 0;  // CTAs the per-CTA scratch is sized for
     // carved pointers
-    int32_t* queues = nullptr;  // [0] build, [1] seed, [2] match; [16, 144) item classes, [144, 272) their fill
+    // [0] build, [1] seed, [2] match queues; fused matching: [3] announced, [4] fault,
+    // [5] claimed, [6] done; [16, 144) item classes, [144, 272) their fill
+    int32_t* queues = nullptr;
     unsigned long long* pool_ctr = nullptr;
     float* cx = nullptr;
     int32_t* corig = nullptr;
@@ -412,6 +414,9 @@ struct Workspace {
     int32_t* item_count = nullptr;
     int32_t* item_class = nullptr;
     int32_t* order = nullptr;
+    int32_t* ev_done = nullptr;    // fused matching: [events] halves done, then [events] announced
+    int32_t* pool_velo = nullptr;  // fused matching: per seed record
+    float* pool_chi2 = nullptr;
 };
 
 struct Pipeline;
@@ -515,6 +520,9 @@ static size_t carve(st_ctx* ctx, Workspace& w, int64_t ne, int64_t nh, int32_t m
     char* ic = take(sizeof(int32_t) * size_t(items) + 4);
     char* icl = take(sizeof(int32_t) * size_t(items) + 4);
     char* ord = take(sizeof(int32_t) * size_t(items) + 4);
+    char* evd = take(sizeof(int32_t) * size_t(items) + 4);
+    char* pv = take(sizeof(int32_t) * size_t(sc) + 4);
+    char* pc = take(sizeof(float) * size_t(sc) + 4);
     if (base) {
         w.queues = reinterpret_cast<int32_t*>(q);
         w.pool_ctr = reinterpret_cast<unsigned long long*>(q + 32);
@@ -533,6 +541,9 @@ static size_t carve(st_ctx* ctx, Workspace& w, int64_t ne, int64_t nh, int32_t m
         w.item_count = reinterpret_cast<int32_t*>(ic);
         w.item_class = reinterpret_cast<int32_t*>(icl);
         w.order = reinterpret_cast<int32_t*>(ord);
+        w.ev_done = reinterpret_cast<int32_t*>(evd);
+        w.pool_velo = reinterpret_cast<int32_t*>(pv);
+        w.pool_chi2 = reinterpret_cast<float*>(pc);
         w.cap_events = ne;
         w.cap_hits = nh;
         w.cap_max_hits = mh;
@@ -653,8 +664,11 @@ extern "C" int st_reserve(st_ctx* ctx, int64_t n_events, int64_t n_hits, int32_t
 // seeding / matching
 // ---------------------------------------------------------------------------
 
+// With V and L (fused): the seeding kernel also matches each event once its
+// two halves are done, and the gather writes the Long tracks too.
 static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S, cudaStream_t s,
-                       int64_t n_hits_total, bool may_alloc) {
+                       int64_t n_hits_total, bool may_alloc, const st_velo* V = nullptr, st_long* L = nullptr,
+                       bool defer = false) {
     int rc = ensure(ctx, w, H.n_events, n_hits_total, H.max_hits_per_event, S.cap, may_alloc);
     if (rc != ST_OK) return rc;
     const st_config& c = ctx->cfg;
@@ -673,6 +687,8 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
         ST_CUDA(ctx, cudaMemsetAsync(S.ev_off, 0, sizeof(int32_t), s));
         return ST_OK;
     }
+    const bool fused = V && L;
+    if (fused) ST_CUDA(ctx, cudaMemsetAsync(w.ev_done, 0, 2 * sizeof(int32_t) * size_t(H.n_events), s));
     BuildArgs b;
     b.n_events = H.n_events;
     b.ev_off = H.ev_off;
@@ -725,6 +741,22 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
     a.order = w.order;
     a.queue = w.queues + 1;
     a.counters = ctx->counters;
+    if (fused) {
+        a.velo_off = V->ev_off;
+        a.velo = V->state;
+        a.velo_smem = ctx->velo_smem;
+        a.defer_match = defer ? 1 : 0;
+        a.ev_done = w.ev_done;
+        a.ready = w.ev_done + H.n_events;
+        a.ready_ctr = w.queues + 3;
+        a.fault = w.queues + 4;
+        a.m_claim = w.queues + 5;
+        a.done_ctr = w.queues + 6;
+        a.pool_velo = w.pool_velo;
+        a.pool_chi2 = w.pool_chi2;
+        a.n_long = L->n_long;
+        if (ctx->timing && &w == &ctx->ws) ctx->tused[3] = false;  // matching runs inside k_seed
+    }
     tmark(ctx, w, 1, 0, s);
     ST_CUDA(ctx, launch_seed(ctx->P, a, g_seed, c.threads_seed, s));
     tmark(ctx, w, 1, 1, s);
@@ -744,6 +776,13 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
     g.state = S.state;
     g.n_hits = S.n_hits;
     g.status = S.status;
+    if (fused) {
+        g.pool_velo = w.pool_velo;
+        g.pool_chi2 = w.pool_chi2;
+        g.velo_idx = L->velo_idx;
+        g.chi2 = L->chi2;
+        g.fault = w.queues + 4;
+    }
     tmark(ctx, w, 2, 0, s);
     ST_CUDA(ctx, launch_gather(g, s));
     tmark(ctx, w, 2, 1, s);
@@ -780,6 +819,25 @@ static int run_matching(st_ctx* ctx, Workspace& w, const st_velo& V, const st_se
     ST_CUDA(ctx, launch_match(ctx->P, m, grid, ctx->cfg.threads_match, s));
     tmark(ctx, w, 3, 1, s);
     return ST_OK;
+}
+
+// Seeding then matching of one batch.  The fused kernel (matching inside the
+// seeding kernel) serves the HLT1 configuration with 256-thread seeding CTAs
+// and no final selection; every other configuration runs the two steps apart.
+static bool fusable(const st_ctx* ctx, const st_hits& H, const st_velo& V) {
+    const st_config& c = ctx->cfg;
+    return c.threads_seed <= 256 && c.iter_mode == 0 && !c.final_sel && V.n_events == H.n_events &&
+           match_smem_bytes(ctx->velo_smem) <= ctx->seed_smem;
+}
+
+// defer: the kernel has the GPU to itself (a graph replay), so CTAs without
+// seeding work may wait for the last events (see k_seed).
+static int run_batch(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S, const st_velo& V, st_long& L,
+                     cudaStream_t s, int64_t n_hits_total, bool may_alloc, bool defer) {
+    if (fusable(ctx, H, V)) return run_seeding(ctx, w, H, S, s, n_hits_total, may_alloc, &V, &L, defer);
+    int rc = run_seeding(ctx, w, H, S, s, n_hits_total, may_alloc);
+    if (rc == ST_OK) rc = run_matching(ctx, w, V, S, L, s);
+    return rc;
 }
 
 static int check_hits(st_ctx* ctx, const st_hits* h) {
@@ -942,8 +1000,7 @@ extern "C" int st_graph_create(st_ctx* ctx, const st_hits* hits, const st_velo* 
     g->ctx = ctx;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = run_seeding(ctx, ctx->ws, *hits, *seeds, cs, bound, false);
-        if (rc == ST_OK) rc = run_matching(ctx, ctx->ws, *velo, *seeds, *out, cs);
+        rc = run_batch(ctx, ctx->ws, *hits, *seeds, *velo, *out, cs, bound, false, true);
         cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
         if (rc == ST_OK && e2 != cudaSuccess) rc = set_err(ctx, ST_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
         if (rc == ST_OK) {
@@ -1223,8 +1280,7 @@ static void launch_slot(st_ctx* ctx, Pipeline& pl, int si, std::unique_lock<std:
     st_seeds Sd{ob->cap, ob->ev_off, ob->hits, ob->params, ob->state, ob->n, ob->status};
     st_velo V{ne, S.d_velo_off, pl.d_velo};
     st_long L{ob->vidx, ob->chi2, ob->n_long, ob->gp};
-    if (rc == ST_OK) rc = run_seeding(ctx, S.ws, H, Sd, st, pl.pc.max_hits_per_slot, false);
-    if (rc == ST_OK) rc = run_matching(ctx, S.ws, V, Sd, L, st);
+    if (rc == ST_OK) rc = run_batch(ctx, S.ws, H, Sd, V, L, st, pl.pc.max_hits_per_slot, false, false);
     ck(cudaMemcpyAsync(S.h_counts, ob->ev_off, 4 * (ne + 1), cudaMemcpyDeviceToHost, st));
     ck(cudaEventRecord(S.ev, st));
     S.rc = rc;
