@@ -633,9 +633,14 @@ __device__ __forceinline__ int pair_window(const DevParams& P, const IterP& I, c
     const float bs = fmaf(I.dz21, t13, x1);
     const float xa = fmaf(I.k3, -sg * ulo, bs), xb = fmaf(I.k3, -sg * uhi, bs);
     const int st2 = szl[I.s2], n2 = szl[I.s2 + 1] - st2;
-    const uint16_t* l2 = lut + I.s2 * kLutBins;
-    lo2 = zlo(X + st2, l2, n2, fminf(xa, xb));
-    return zhi(X + st2, l2, n2, fmaxf(xa, xb)) - lo2;
+    const float* x2 = X + st2;
+    lo2 = zlo(x2, lut + I.s2 * kLutBins, n2, fminf(xa, xb));
+    // the window is narrow (most hold no hit): its end by a forward scan
+    // from its start, not a second table search
+    const float hi = fmaxf(xa, xb);
+    int e = lo2;
+    while (e < n2 && !(hi < x2[e])) ++e;
+    return e - lo2;
 }
 
 constexpr int kTripPerCand = 2;  // triplet buffer entries per candidate slot
@@ -1353,8 +1358,9 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ GatherArg
 // two (event, half) items and go to one contiguous range of each output
 // array, so every array is copied as a flat run (16-byte words when all
 // output arrays allow it).
+// (at most 32 registers: eight CTAs per SM, a 1000-event batch in one round)
 template <bool kVec>
-__global__ void __launch_bounds__(256) k_gather(const __grid_constant__ GatherArgs A) {
+__global__ void __launch_bounds__(256, 8) k_gather(const __grid_constant__ GatherArgs A) {
     const bool fault = A.fault && *A.fault;
     for (int64_t e = blockIdx.x; e < A.n_events; e += gridDim.x) {
         if (fault && threadIdx.x == 0) A.status[e] = -4;  // ST_TIMEOUT: the fused matching gave up a wait
@@ -1364,32 +1370,65 @@ __global__ void __launch_bounds__(256) k_gather(const __grid_constant__ GatherAr
         const int64_t s0 = A.item_start[2 * e], s1 = A.item_start[2 * e + 1];
         const int64_t d0 = A.ev_off[e];
         auto src = [&](int k) { return k < c0 ? s0 + k : s1 + (k - c0); };
-        if (A.pool_velo) {
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                A.velo_idx[d0 + k] = A.pool_velo[src(k)];
-                A.chi2[d0 + k] = A.pool_chi2[src(k)];
-            }
-        }
+        const int T = blockDim.x;
         if (kVec) {
+            // the event's 16-byte words as one range: hits (3 per record),
+            // params (2), state (1); a thread loads four words before it stores
+            // them, so their latencies overlap
             const uint4* ph = reinterpret_cast<const uint4*>(A.pool_hits);
             const uint4* pp = reinterpret_cast<const uint4*>(A.pool_params);
             const uint4* ps = reinterpret_cast<const uint4*>(A.pool_state);
             uint4* oh = reinterpret_cast<uint4*>(A.hits);
             uint4* op = reinterpret_cast<uint4*>(A.params);
             uint4* os = reinterpret_cast<uint4*>(A.state);
-            for (int i = threadIdx.x; i < 3 * n; i += blockDim.x) {
-                const int k = i / 3, q = i - 3 * k;
-                oh[(d0 + k) * 3 + q] = ph[src(k) * 3 + q];
+            const int W = 6 * n;
+            for (int w0 = threadIdx.x; w0 < W; w0 += 4 * T) {
+                uint4 v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int w = w0 + j * T;
+                    if (w < 3 * n) {
+                        const int k = w / 3;
+                        v[j] = ph[src(k) * 3 + (w - 3 * k)];
+                    } else if (w < 5 * n) {
+                        const int u = w - 3 * n;
+                        v[j] = pp[src(u >> 1) * 2 + (u & 1)];
+                    } else if (w < W) {
+                        v[j] = ps[src(w - 5 * n)];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int w = w0 + j * T;
+                    if (w < 3 * n) {
+                        oh[d0 * 3 + w] = v[j];
+                    } else if (w < 5 * n) {
+                        op[d0 * 2 + (w - 3 * n)] = v[j];
+                    } else if (w < W) {
+                        os[d0 + (w - 5 * n)] = v[j];
+                    }
+                }
             }
-            for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) {
-                const int k = i >> 1, q = i & 1;
-                op[(d0 + k) * 2 + q] = pp[src(k) * 2 + q];
-            }
-            for (int k = threadIdx.x; k < n; k += blockDim.x) os[d0 + k] = ps[src(k)];
             const uint16_t* pn = reinterpret_cast<const uint16_t*>(A.pool_n);
             uint16_t* on = reinterpret_cast<uint16_t*>(A.n_hits);
-            for (int k = threadIdx.x; k < n; k += blockDim.x) on[d0 + k] = pn[src(k)];
+            for (int k = threadIdx.x; k < n; k += T) {
+                const int64_t r = src(k);
+                const uint16_t c = pn[r];
+                if (A.pool_velo) {
+                    const int32_t vi = A.pool_velo[r];
+                    const float ch = A.pool_chi2[r];
+                    A.velo_idx[d0 + k] = vi;
+                    A.chi2[d0 + k] = ch;
+                }
+                on[d0 + k] = c;
+            }
         } else {
+            if (A.pool_velo) {
+                for (int k = threadIdx.x; k < n; k += T) {
+                    A.velo_idx[d0 + k] = A.pool_velo[src(k)];
+                    A.chi2[d0 + k] = A.pool_chi2[src(k)];
+                }
+            }
             for (int i = threadIdx.x; i < 12 * n; i += blockDim.x) {
                 const int k = i / 12, q = i - 12 * k;
                 A.hits[(d0 + k) * 12 + q] = A.pool_hits[src(k) * 12 + q];
