@@ -619,10 +619,10 @@ __device__ __forceinline__ ull pack_trip(int it, int k1, int k3, int k2) {
     return (ull(it) << 60) | (ull(k1) << 40) | (ull(k3) << 20) | ull(k2);
 }
 
-// The two-hit / third-hit windows of one pair: first T2 index and count.
-__device__ __forceinline__ int pair_window(const DevParams& P, const IterP& I, const float* X,
-                                           const int* szl, const uint16_t* lut, float x1, float x3,
-                                           int& lo2) {
+// The two-hit / third-hit windows of one pair: first T2 index and count
+// (x2, l2, n2: the T2 slot's hits, bucket table and size).
+__device__ __forceinline__ int pair_window(const DevParams& P, const IterP& I, const float* x2,
+                                           const uint16_t* l2, int n2, float x1, float x3, int& lo2) {
     const float t13 = (x3 - x1) * I.inv_dz31;
     const float x0 = fmaf(-I.z1, t13, x1);
     const float ip = fmaf(P.invp_b * x0, x0, P.invp_a * fabsf(x0));
@@ -632,9 +632,7 @@ __device__ __forceinline__ int pair_window(const DevParams& P, const IterP& I, c
     const float ulo = fmaf(I.mlo_k, ip, -I.c0), uhi = fmaf(I.mhi_k, ip, I.c0);
     const float bs = fmaf(I.dz21, t13, x1);
     const float xa = fmaf(I.k3, -sg * ulo, bs), xb = fmaf(I.k3, -sg * uhi, bs);
-    const int st2 = szl[I.s2], n2 = szl[I.s2 + 1] - st2;
-    const float* x2 = X + st2;
-    lo2 = zlo(x2, lut + I.s2 * kLutBins, n2, fminf(xa, xb));
+    lo2 = zlo(x2, l2, n2, fminf(xa, xb));
     // the window is narrow (most hold no hit): its end by a forward scan
     // from its start, not a second table search
     const float hi = fmaxf(xa, xb);
@@ -962,6 +960,8 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 int k3 = sA[o] + (pb - sPS[o]);
                 int tg = sB[o];
                 int it = tg >> 20, k1 = tg & 0xFFFFF;
+                // the owner's iteration's slot starts, kept while the owner lasts
+                int st3 = szl[P.it[it].s3], st2 = szl[P.it[it].s2], n2 = szl[P.it[it].s2 + 1] - st2;
                 float x1 = X[szl[P.it[it].s1] + k1];
                 for (int p = pb; p < pe; ++p) {
                     while (p >= nxt) {
@@ -971,13 +971,17 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                         tg = sB[o];
                         it = tg >> 20;
                         k1 = tg & 0xFFFFF;
+                        st3 = szl[P.it[it].s3];
+                        st2 = szl[P.it[it].s2];
+                        n2 = szl[P.it[it].s2 + 1] - st2;
                         x1 = X[szl[P.it[it].s1] + k1];
                     }
                     const IterP& I = P.it[it];
                     int lo2 = 0, c = 0;
-                    if (!is_used(used, szl[I.s3] + k3)) c = pair_window(P, I, X, szl, lut, x1, X[szl[I.s3] + k3], lo2);
+                    if (!is_used(used, st3 + k3))
+                        c = pair_window(P, I, X + st2, lut + I.s2 * kLutBins, n2, x1, X[st3 + k3], lo2);
                     for (int q = 0; q < c; ++q) {
-                        if (is_used(used, szl[I.s2] + lo2 + q)) continue;
+                        if (is_used(used, st2 + lo2 + q)) continue;
                         const ull key = pack_trip(it, k1, k3, lo2 + q);
                         if (direct) trip[wofs + w] = key;
                         else if (w < kTripLocal) tloc[w * T] = key;
