@@ -9,7 +9,8 @@ flushed (256 MB write) between timed steps, outside the timed interval.
 
 Reported beside the batched number (one JSON line on stdout):
   e2e           the same batch through pipeline_submit / pipeline_poll with
-                host buffers (copies in the timed region), three batches in flight
+                pinned host buffers (copies in the timed region), three batches
+                in flight; also with pageable buffers
   per_event     the plain per-event launch: seeding_run + matching_run per
                 event on one stream
   served        continuous batching of a Poisson request stream (batch sizes
@@ -287,8 +288,10 @@ def main():
     cap = max(1024, batch.n_hits // 4)
     out = st.DeviceOutputs(n_ev, cap, device=dev)
     ctx.st_reserve(n_ev, n_ev * db.max_hits, db.max_hits, cap)
-    ctx.st_set_timing(True)
     stream = torch.cuda.Stream(device=dev)
+    # the timed graph carries no timing marks (they add nodes to every
+    # replay); the per-kernel times come from a second graph that does
+    ctx.st_set_timing(False)
     graph = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     # build, order, seed, scan, gather, and match unless the matching runs
@@ -305,7 +308,7 @@ def main():
         ctx.st_read_counters(reset=True)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
-        step_ms, kms = [], {"build": 0.0, "seed": 0.0, "gather": 0.0, "match": 0.0}
+        step_ms = []
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -316,11 +319,10 @@ def main():
             ev1.record(stream)
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
-            for k, v in ctx.st_kernel_ms().items():
-                kms[k] += v
         torch.cuda.synchronize()
         clk = clocks.stop()
     counters = ctx.st_read_counters(reset=True)
+    kms = {k: v * args.steps for k, v in kernel_times(ctx, db, out, flush, stream, args.steps).items()}
     total_ms = float(np.sum(step_ms))
     log(f"batched: {np.mean(step_ms):.3f} ms/step, kernels {kms}")
     total_ms = max_over_ranks(total_ms, device=dev)
@@ -414,36 +416,43 @@ def main():
     ctx2.st_pipeline_configure(n_slots=3, max_events_per_slot=n_ev, max_hits_per_slot=batch.n_hits + 16,
                                max_hits_per_event=db.max_hits, max_velo_per_event=1024,
                                max_velo_per_slot=int(batch.velo.shape[0]) + 16)
-    hh, hv, keep = st.HostBuffers.inputs(batch.ev_off, batch.x, batch.zone, batch.velo_off, batch.velo)
-    hb = st.HostBuffers(n_ev, cap)
-    for _ in range(2):
-        t = ctx2.pipeline_submit(hh, hv)
-        rc, _ = ctx2.pipeline_poll(t, hb.seeds, hb.long, 60_000_000)
-        assert rc == st.ST_OK, rc
     h2d = 8 * (n_ev + 1) * 2 + 8 * batch.n_hits + 16 * batch.velo.shape[0]
-    # three batches in flight: the next batches' inputs are copied in while the
-    # current one runs; every step's results are read back to the host
-    depth = 3
-    pending = []
-    if ws > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        pending.append(ctx2.pipeline_submit(hh, hv))
-        if len(pending) >= depth:
+
+    def e2e_run(pinned):
+        """Seconds for args.steps batches through submit / poll, three in
+        flight: the next batches' inputs are copied in while the current one
+        runs; every step's results are read back to the host."""
+        hh, hv, keep = st.HostBuffers.inputs(batch.ev_off, batch.x, batch.zone, batch.velo_off, batch.velo,
+                                             pinned=pinned)
+        hb = st.HostBuffers(n_ev, cap, pinned=pinned)
+        for _ in range(2):
+            t = ctx2.pipeline_submit(hh, hv)
+            rc, _ = ctx2.pipeline_poll(t, hb.seeds, hb.long, 60_000_000)
+            assert rc == st.ST_OK, rc
+        depth, pending = 3, []
+        if ws > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pending.append(ctx2.pipeline_submit(hh, hv))
+            if len(pending) >= depth:
+                rc, info = ctx2.pipeline_poll(pending.pop(0), hb.seeds, hb.long, 60_000_000)
+                assert rc == st.ST_OK, rc
+        while pending:
             rc, info = ctx2.pipeline_poll(pending.pop(0), hb.seeds, hb.long, 60_000_000)
             assert rc == st.ST_OK, rc
-    while pending:
-        rc, info = ctx2.pipeline_poll(pending.pop(0), hb.seeds, hb.long, 60_000_000)
-        assert rc == st.ST_OK, rc
-    e2e_total = time.perf_counter() - t0
-    ns = int(hb.ev_off[-1])
+        return time.perf_counter() - t0, int(hb.ev_off[-1])
+
+    e2e_pageable, _ = e2e_run(False)
+    e2e_total, ns = e2e_run(True)
     d2h = 4 * (n_ev + 1) + 8 * n_ev + ns * (48 + 32 + 16 + 2 + 8)
     e2e_total = max_over_ranks(e2e_total, device=dev)
-    log(f"e2e: {1000 * e2e_total / args.steps:.3f} ms/step")
+    e2e_pageable = max_over_ranks(e2e_pageable, device=dev)
+    log(f"e2e: {1000 * e2e_total / args.steps:.3f} ms/step (pageable {1000 * e2e_pageable / args.steps:.3f})")
     result["e2e"] = {"value": job_rate(n_ev * args.steps, ws, e2e_total), "unit": "events/s",
                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                     "api": "pipeline_submit + pipeline_poll, pageable host buffers, three batches in flight"}
+                     "api": "pipeline_submit + pipeline_poll, pinned host buffers, three batches in flight",
+                     "pageable_value": job_rate(n_ev * args.steps, ws, e2e_pageable)}
 
     if rank == 0 and ws == 1:
         # ---------------- plain per-event launch
@@ -512,17 +521,31 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def time_variant(st, overrides, db, out, cap, n_ev, flush, stream, steps, nn=None):
-    """Batched graph replay of the same device batch under another method
-    configuration: events/s and per-kernel times."""
+def kernel_times(ctx, db, out, flush, stream, steps):
+    """Mean per-kernel times (CUDA events around each kernel, recorded by the
+    library inside a graph of the same batch captured with timing marks)."""
     import torch
-    ctx = st.Context(st.st_config_default(**overrides), device=db.x.device.index or 0)
-    if nn is not None:
-        ctx.st_set_ghost_nn(nn)
-    ctx.st_reserve(n_ev, n_ev * db.max_hits, db.max_hits, cap)
     ctx.st_set_timing(True)
     g = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
+    n = max(3, steps // 2)
     kms = {}
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            g.st_graph_launch(stream)
+        for _ in range(n):
+            flush.fill_(1)
+            g.st_graph_launch(stream)
+            stream.synchronize()
+            for k, v in ctx.st_kernel_ms().items():
+                kms[k] = kms.get(k, 0.0) + v / n
+    g.close()
+    ctx.st_set_timing(False)
+    return kms
+
+
+def replay_ms(g, flush, stream, steps):
+    """Mean time of one replay of graph g (L2 flushed before each)."""
+    import torch
     with torch.cuda.stream(stream):
         for _ in range(3):
             g.st_graph_launch(stream)
@@ -535,12 +558,24 @@ def time_variant(st, overrides, db, out, cap, n_ev, flush, stream, steps, nn=Non
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-            for k, v in ctx.st_kernel_ms().items():
-                kms[k] = kms.get(k, 0.0) + v / steps
+    return tot / steps
+
+
+def time_variant(st, overrides, db, out, cap, n_ev, flush, stream, steps, nn=None):
+    """Batched graph replay of the same device batch under another method
+    configuration: events/s and per-kernel times."""
+    import torch
+    ctx = st.Context(st.st_config_default(**overrides), device=db.x.device.index or 0)
+    if nn is not None:
+        ctx.st_set_ghost_nn(nn)
+    ctx.st_reserve(n_ev, n_ev * db.max_hits, db.max_hits, cap)
+    g = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
+    ms = replay_ms(g, flush, stream, steps)
     seeds = int(out.ev_off[-1].item())
     g.close()
+    kms = kernel_times(ctx, db, out, flush, stream, steps)
     ctx.close()
-    return {"value": n_ev * steps / (tot / 1000.0), "unit": "events/s", "ms_per_step": tot / steps,
+    return {"value": n_ev / (ms / 1000.0), "unit": "events/s", "ms_per_step": ms,
             "kernel_ms": kms, "seeds_per_event": seeds / n_ev,
             "config": {k: v for k, v in overrides.items() if k != "zmx"}}
 
@@ -557,28 +592,14 @@ def time_uneven(st, cfg, local, flush, stream, steps):
     out = st.DeviceOutputs(b.n_events, cap, device=dev)
     ctx = st.Context(cfg, device=local)
     ctx.st_reserve(b.n_events, b.n_events * db.max_hits, db.max_hits, cap)
-    ctx.st_set_timing(True)
     g = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
-    kms = {}
     n = max(3, steps // 4)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            g.st_graph_launch(stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        tot = 0.0
-        for _ in range(n):
-            flush.fill_(1)
-            e0.record(stream)
-            g.st_graph_launch(stream)
-            e1.record(stream)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-            for k, v in ctx.st_kernel_ms().items():
-                kms[k] = kms.get(k, 0.0) + v / n
+    ms = replay_ms(g, flush, stream, n)
     ok = int((out.status[: b.n_events] == 0).sum())
     g.close()
+    kms = kernel_times(ctx, db, out, flush, stream, n)
     ctx.close()
-    return {"value": b.n_events * n / (tot / 1000.0), "unit": "events/s", "ms_per_step": tot / n,
+    return {"value": b.n_events / (ms / 1000.0), "unit": "events/s", "ms_per_step": ms,
             "events": b.n_events, "hits_per_event": b.n_hits / b.n_events,
             "max_hits_per_event": int(np.max(np.diff(b.ev_off))), "events_ok": ok, "kernel_ms": kms}
 

@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(kOrderThreads) k_order(const __grid_constant__
     __syncthreads();
     const int64_t items = 2 * A.n_events;
     const int64_t i = int64_t(blockIdx.x) * kOrderThreads + tid;
+    if (A.zero2 && i < items) A.zero2[i] = 0;
     const int c = i < items ? A.item_class[i] : -1;
     const unsigned same = __match_any_sync(0xffffffffu, c);
     const int leader = __ffs(same) - 1;

@@ -35,6 +35,7 @@ struct BuildArgs {
     int32_t* class_count; // [128] items per class, zero before the launch
     int32_t* class_fill;  // [128] places taken per class, zero before the launch
     int32_t* order;       // [2 n_events] the seeding items, costliest class first
+    int32_t* zero2 = nullptr;  // [2 n_events] cleared by k_order (fused matching's counters), may be null
     int32_t* queue;
     unsigned long long* counters;
 };

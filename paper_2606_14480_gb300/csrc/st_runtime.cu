@@ -688,7 +688,6 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
         return ST_OK;
     }
     const bool fused = V && L;
-    if (fused) ST_CUDA(ctx, cudaMemsetAsync(w.ev_done, 0, 2 * sizeof(int32_t) * size_t(H.n_events), s));
     BuildArgs b;
     b.n_events = H.n_events;
     b.ev_off = H.ev_off;
@@ -710,6 +709,7 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
     b.class_count = w.queues + 16;
     b.class_fill = w.queues + 16 + 128;
     b.order = w.order;
+    b.zero2 = fused ? w.ev_done : nullptr;  // halves done + announcements, cleared before k_seed
     b.queue = w.queues + 0;
     b.counters = ctx->counters;
     tmark(ctx, w, 0, 0, s);

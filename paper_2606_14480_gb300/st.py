@@ -401,33 +401,55 @@ class DeviceOutputs:
                 "ut_n": self.ut_n[:ns].cpu().numpy(), "ut_gamma": self.ut_gamma[:ns].cpu().numpy()}
 
 
+def _host_array(a_or_shape, dtype, pinned: bool, keep: list):
+    """A numpy array in host memory, page-locked (through a pinned torch
+    tensor kept in `keep`) if `pinned`; a copy of `a_or_shape` when it is an
+    array, else zero-filled of that shape."""
+    src = None if isinstance(a_or_shape, tuple) else np.ascontiguousarray(a_or_shape, dtype)
+    shape = a_or_shape if src is None else src.shape
+    if not pinned:
+        return np.zeros(shape, dtype) if src is None else src
+    import torch
+    t = torch.zeros(shape, dtype=torch.from_numpy(np.zeros(0, dtype)).dtype, pin_memory=True)
+    keep.append(t)
+    a = t.numpy()
+    if src is not None:
+        a[...] = src
+    return a
+
+
 class HostBuffers:
     """Host (numpy) buffers for the pipeline: inputs of pipeline_submit and
-    outputs of pipeline_poll."""
+    outputs of pipeline_poll; page-locked with pinned=True (the copies then
+    run at the link's full rate)."""
 
     @staticmethod
-    def inputs(ev_off, x, zone, velo_off, velo, max_hits=65535):
-        keep = [np.ascontiguousarray(ev_off, np.int64), np.ascontiguousarray(x, np.float32),
-                np.ascontiguousarray(zone, np.int32), np.ascontiguousarray(velo_off, np.int64),
-                np.ascontiguousarray(np.asarray(velo, np.float32).reshape(-1, 4))]
+    def inputs(ev_off, x, zone, velo_off, velo, max_hits=65535, pinned=False):
+        pins = []
+        keep = [_host_array(ev_off, np.int64, pinned, pins), _host_array(x, np.float32, pinned, pins),
+                _host_array(zone, np.int32, pinned, pins), _host_array(velo_off, np.int64, pinned, pins),
+                _host_array(np.asarray(velo, np.float32).reshape(-1, 4), np.float32, pinned, pins)]
+        keep += pins
         n = len(ev_off) - 1
         p = lambda a: a.ctypes.data
         hits = StHits(n, p(keep[0]), p(keep[1]), p(keep[2]), None, None, max_hits, 0)
         velo_s = StVelo(n, p(keep[3]), p(keep[4]))
         return hits, velo_s, keep
 
-    def __init__(self, n_events: int, cap: int):
-        # filled by pipeline_poll up to the returned counts; not zeroed
-        self.ev_off = np.zeros(n_events + 1, np.int32)
-        self.hits = np.empty((max(cap, 1), 12), np.int32)
-        self.params = np.empty((max(cap, 1), 8), np.float32)
-        self.state = np.empty((max(cap, 1), 4), np.float32)
-        self.n_hits = np.empty((max(cap, 1), 2), np.int8)
-        self.status = np.zeros(max(n_events, 1), np.int32)
-        self.velo_idx = np.empty(max(cap, 1), np.int32)
-        self.chi2 = np.empty(max(cap, 1), np.float32)
-        self.n_long = np.zeros(max(n_events, 1), np.int32)
-        self.ghost_prob = np.empty(max(cap, 1), np.float32)
+    def __init__(self, n_events: int, cap: int, pinned: bool = False):
+        # filled by pipeline_poll up to the returned counts
+        self._pins = []
+        h = lambda shape, dt: _host_array(shape, dt, pinned, self._pins)
+        self.ev_off = h((n_events + 1,), np.int32)
+        self.hits = h((max(cap, 1), 12), np.int32)
+        self.params = h((max(cap, 1), 8), np.float32)
+        self.state = h((max(cap, 1), 4), np.float32)
+        self.n_hits = h((max(cap, 1), 2), np.int8)
+        self.status = h((max(n_events, 1),), np.int32)
+        self.velo_idx = h((max(cap, 1),), np.int32)
+        self.chi2 = h((max(cap, 1),), np.float32)
+        self.n_long = h((max(n_events, 1),), np.int32)
+        self.ghost_prob = h((max(cap, 1),), np.float32)
         p = lambda a: a.ctypes.data
         self.seeds = StSeeds(cap, p(self.ev_off), p(self.hits), p(self.params), p(self.state), p(self.n_hits),
                              p(self.status))
