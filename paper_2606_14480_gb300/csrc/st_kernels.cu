@@ -87,8 +87,8 @@ size_t build_smem_bytes(int bins, int smem_hits) {
     return align16(sizeof(int) * (2 * NB + 1 + 36)) + align16(size_t(10) * smem_hits);
 }
 
-// at most 40 registers: three 512-thread CTAs per SM
-__global__ void __launch_bounds__(kMaxThreads, 3)
+// at most 32 registers: four 512-thread CTAs per SM (a 1000-event batch in two rounds)
+__global__ void __launch_bounds__(kMaxThreads, 4)
 k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = A.bins, NB = kZones * B, T = blockDim.x, tid = threadIdx.x;
