@@ -96,12 +96,16 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
     int* off = cnt + NB;
     int* tmp = off + NB + 1;
     unsigned char* harea = smem + align16(sizeof(int) * (2 * NB + 1 + 36));
+    // s_item: the CTA's next event.  Thread 0 takes its queue ticket while the
+    // current event is still being sorted (during the placement; it is
+    // published at the end), so the atomic's round trip does not stand
+    // between two events.
     __shared__ int s_item, s_bad;
     ull ctr[2] = {0, 0};
+    int q_next = 0;
+    if (tid == 0) s_item = atomicAdd(A.queue, 1);
 
     for (;;) {
-        __syncthreads();
-        if (tid == 0) s_item = atomicAdd(A.queue, 1);
         __syncthreads();
         const int64_t e = s_item;
         if (e >= A.n_events) break;
@@ -112,6 +116,8 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
             for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
             if (tid == 0) A.status[e] = -3;  // ST_OVERFLOW
             if (tid < 2) set_item_class(A, 2 * e + tid, 0);
+            __syncthreads();  // every thread has read s_item
+            if (tid == 0) s_item = atomicAdd(A.queue, 1);
             continue;
         }
         const int n = static_cast<int>(n64);
@@ -120,6 +126,8 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
             for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
             if (tid == 0) A.status[e] = -3;  // ST_OVERFLOW
             if (tid < 2) set_item_class(A, 2 * e + tid, 0);
+            __syncthreads();
+            if (tid == 0) s_item = atomicAdd(A.queue, 1);
             continue;
         }
         const bool in_smem = n <= A.smem_hits;
@@ -172,6 +180,7 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
             for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
             if (tid == 0) A.status[e] = -1;  // ST_EINVAL
             if (tid < 2) set_item_class(A, 2 * e + tid, 0);
+            if (tid == 0) s_item = atomicAdd(A.queue, 1);  // s_item was read before the barrier above
             continue;
         }
         {   // exclusive scan of the bucket counts
@@ -188,8 +197,11 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
             if (tid == 0) off[NB] = tot;
         }
         __syncthreads();
+        if (tid == 0) q_next = atomicAdd(A.queue, 1);  // published after the output
         for (int i = tid; i < n; i += T) pm[off[bk[i]] + rk[i]] = static_cast<uint16_t>(i);
         __syncthreads();
+        // rank of each hit in its bucket -> its place in the sorted event, kept
+        // in rk (which no other thread reads from here on)
         for (int i = tid; i < n; i += T) {
             const int b = bk[i], s = off[b], c = cnt[b];
             const float x = hx[i];
@@ -199,8 +211,17 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
                 const float xj = hx[j];
                 r += (xj < x) || (xj == x && j < i);
             }
-            A.cx[cb + s + r] = x;
-            A.corig[cb + s + r] = i;
+            rk[i] = static_cast<uint16_t>(s + r);
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += T) pm[rk[i]] = static_cast<uint16_t>(i);
+        __syncthreads();
+        // the sorted event goes out in order (coalesced stores; scattered
+        // stores from the ranking took a third of the kernel's time)
+        for (int d = tid; d < n; d += T) {
+            const int i = pm[d];
+            A.cx[cb + d] = hx[i];
+            A.corig[cb + d] = i;
         }
         for (int k = tid; k < kZoffStride; k += T) zo[k] = off[k * B];
         if (tid < 2) {
@@ -213,6 +234,7 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
             A.status[e] = 0;
             ctr[0] += n;
             ctr[1] += 1;
+            s_item = q_next;
         }
     }
     flush_counters(A.counters + C_HITS, ctr, 2);
