@@ -776,7 +776,10 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     if (kFuse && tid < 3) s_mctr[tid] = 0;
     int spar = 0;  // which half of tmp the next block scan uses
 
-    ull ctr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // work counters (pairs, triplets, extended, candidates, kept, UV initial
+    // hits, valid UV chains, seeds): block totals, added up by thread 0
+    __shared__ ull s_ctr[8];
+    if (tid < 8) s_ctr[tid] = 0;
 
     int64_t fin = -1;  // fused: event of the half this CTA finished last
     for (;;) {
@@ -962,9 +965,9 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 if (is_used(used, szl[I.s1] + k1)) np = 0;
                 tag = (it << 20) | k1;
             }
-            ctr[0] += np;
             int tot_p;
             const int ps = block_exscan1(np, tmp, spar, tot_p);
+            if (tid == 0) s_ctr[0] += tot_p;
             sPS[tid] = ps;
             sA[tid] = lo3;
             sB[tid] = tag;
@@ -1018,7 +1021,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             int tot_t;
             bool again;
             int wofs = block_exscan1_any(nt, nt > kTripLocal, tmp, spar, tot_t, again);
-            ctr[1] += nt;
+            if (tid == 0) s_ctr[1] += tot_t;
             if (ntrip + tot_t > TC) overflow = true;
             if (!overflow) {
                 wofs += ntrip;
@@ -1042,10 +1045,13 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     const int it = static_cast<int>(tk >> 60);
                     code = do_triplet(P, P.it[it], X, szl, lut, sG, sMask, used, static_cast<int>((tk >> 40) & 0xFFFFF),
                                       static_cast<int>(tk & 0xFFFFF), static_cast<int>((tk >> 20) & 0xFFFFF), o);
-                    ctr[2] += code >= 1;
                 }
+                // candidates in the low 16 bits, extended triplets (code >= 1)
+                // in the high ones: at most one each per thread, so no carry
                 int tot;
-                const int co = block_exscan1(code == 2 ? 1 : 0, tmp, spar, tot);
+                const int co = block_exscan1((code == 2 ? 1 : 0) | (code >= 1 ? 0x10000 : 0), tmp, spar, tot) & 0xFFFF;
+                if (tid == 0) s_ctr[2] += tot >> 16;
+                tot &= 0xFFFF;
                 if (code == 2) {
                     const int ci = ncand + co;
                     if (ci < CC) {
@@ -1102,7 +1108,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             if (keep) kept[nk + o] = k;
             nk += tot;
         }
-        if (tid == 0) ctr[4] += nk - kb;
+        if (tid == 0) s_ctr[4] += nk - kb;
         __syncthreads();
 
         // ------------------------------------------------------------ UV
@@ -1146,9 +1152,9 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 lo = zlo(X + st, lz, n, fminf(xa, xb));
                 cntc = zhi(X + st, lz, n, fmaxf(xa, xb)) - lo;
             }
-            ctr[5] += cntc;
             int tot;
             const int ps = block_exscan1(cntc, tmp, spar, tot);
+            if (tid == 0) s_ctr[5] += tot;
             sPS[tid] = ps;
             sA[tid] = lo;
             sB[tid] = i;
@@ -1178,7 +1184,6 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                         uv_chain(P, X, szl, lut, used, Xs + 6 * j, pass, kinit, u);
                     }
                     if (u.n >= P.n_uv_min) {
-                        ++ctr[6];
                         const int sidx = atomicAdd(&s_nvalid, 1);
                         if (sidx < kUvStore) {
                             uint4 r;
@@ -1253,7 +1258,10 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             __syncthreads();
         }
         }  // passes
-        if (tid == 0) ctr[3] += ncand;
+        if (tid == 0) {
+            s_ctr[3] += ncand;
+            s_ctr[6] += s_nvalid;  // every valid UV chain of the item's passes
+        }
         if (overflow || (seq && s_nvalid > kUvStore)) {
             if (tid == 0) {
                 A.status[e] = -3;  // ST_OVERFLOW
@@ -1284,7 +1292,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             s_start = st;
             A.item_start[item] = st == ~0ull ? 0 : static_cast<int32_t>(st);
             A.item_count[item] = st == ~0ull ? 0 : nseed;
-            ctr[7] += st == ~0ull ? 0 : nseed;
+            s_ctr[7] += st == ~0ull ? 0 : nseed;
         }
         __syncthreads();
         if (s_start == ~0ull) continue;
@@ -1359,7 +1367,8 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             wbase += tot;
         }
     }
-    flush_counters(A.counters + C_PAIRS, ctr, 8);
+    __syncthreads();
+    if (tid < 8 && s_ctr[tid]) atomicAdd(A.counters + C_PAIRS + tid, s_ctr[tid]);
     if (kFuse && tid < 3 && s_mctr[tid]) atomicAdd(A.counters + C_MATCH_PAIRS + tid, s_mctr[tid]);
 }
 
