@@ -152,7 +152,7 @@ extern "C" int seeding_run_static(const st_config* cfg, const st_hits* H, st_see
     const size_t bsmem = build_smem_bytes(bins, static_cast<int>(mh));
     const int bbps = std::max(1, build_blocks_per_sm(cfg->threads_build, bsmem));
     const int g_build = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ne, int64_t(D->n_sms) * bbps)));
-    const int tbl_smem = cfg->smem_hits / 2, key_smem = std::max(64, cfg->smem_hits / 4);
+    const int tbl_smem = cfg->smem_hits / 2, key_smem = std::max(64, cfg->smem_hits / 6);  // as st_create
     const size_t ssmem = seed_smem_bytes(cfg->threads_seed, cfg->smem_hits, tbl_smem, key_smem);
     const int sbps = std::max(1, seed_blocks_per_sm(cfg->threads_seed, ssmem));
     const int g_seed = static_cast<int>(
