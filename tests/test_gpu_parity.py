@@ -245,6 +245,69 @@ def test_edge_cases(zmx):
     ctx.close()
 
 
+def test_bad_events_among_many(zmx):
+    """More events than the container-build CTAs (608 on a GB300) with
+    invalid and oversized events spread among them, so that CTAs take further
+    events after rejecting one: every good event's seeds and Long tracks equal
+    those of the same event in a batch without the bad ones, directly and
+    through the CUDA graph (the fused matching)."""
+    b = workload("tiny", n_events=1500)
+    _, gcfg = parity.config_pair(zmx)
+    ev = b.ev_off
+    mh = int(np.diff(ev).max())
+    xs, zs, offs, kinds = [], [], [0], []
+    for e in range(b.n_events):
+        x = b.x[ev[e]:ev[e + 1]].copy()
+        zn = b.zone[ev[e]:ev[e + 1]].copy()
+        kind = "ok"
+        if len(x) and e % 7 == 3:
+            zn[len(zn) // 2] = 24
+            kind = "bad_zone"
+        elif len(x) and e % 11 == 5:
+            x[-1] = np.inf
+            kind = "inf"
+        elif len(x) and e % 13 == 8:
+            reps = mh // len(x) + 1
+            x, zn = np.tile(x, reps)[:mh + 1], np.tile(zn, reps)[:mh + 1]
+            kind = "oversized"
+        xs.append(x)
+        zs.append(zn)
+        offs.append(offs[-1] + len(x))
+        kinds.append(kind)
+    assert kinds.count("ok") > 1000
+    want = {"ok": 0, "bad_zone": -1, "inf": -1, "oversized": -3}
+
+    ctx = st.Context(gcfg)
+    clean = st.run_batch(ctx, st.DeviceBatch.from_synth(b, max_hits=mh))
+    torch.cuda.synchronize()
+    ref = clean.to_numpy()
+    assert (ref["status"] == 0).all()
+    db = st.DeviceBatch(np.array(offs), np.concatenate(xs), np.concatenate(zs), b.velo_off, b.velo, max_hits=mh)
+    direct = st.run_batch(ctx, db)
+    torch.cuda.synchronize()
+    res_direct = direct.to_numpy()
+    cap = int(ref["ev_off"][-1]) + 1024
+    out = st.DeviceOutputs(b.n_events, cap)
+    ctx.st_reserve(b.n_events, b.n_events * mh, mh, cap)
+    g = ctx.st_graph_create(db.hits, db.velo_s, out.seeds, out.long)
+    g.st_graph_launch()
+    torch.cuda.synchronize()
+    res_graph = out.to_numpy()
+    g.close()
+    ctx.close()
+    for res in (res_direct, res_graph):
+        for e, kind in enumerate(kinds):
+            assert res["status"][e] == want[kind], (e, kind, res["status"][e])
+            s0, s1 = res["ev_off"][e], res["ev_off"][e + 1]
+            if kind != "ok":
+                assert s1 == s0 and res["n_long"][e] == 0
+                continue
+            r0, r1 = ref["ev_off"][e], ref["ev_off"][e + 1]
+            assert np.array_equal(res["hits"][s0:s1], ref["hits"][r0:r1]), e
+            assert np.array_equal(res["velo_idx"][s0:s1], ref["velo_idx"][r0:r1]), e
+            assert res["n_long"][e] == ref["n_long"][e], e
+
+
 def test_empty_batch():
     ctx = st.Context(st.st_config_default())
     db = st.DeviceBatch(np.zeros(1, np.int64), np.zeros(0, np.float32), np.zeros(0, np.int32),
