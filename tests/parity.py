@@ -6,13 +6,20 @@ event-local hit indices):
     must be at least AGREE_MIN (99.9%);
   * every seed in only one of the two sets must be traced to an oracle ledger
     decision whose margin is at most TAU (1e-5, relative to the magnitude of
-    the numbers that decision is made from): the seed shares a hit with that
-    decision, or with an oracle x-z candidate that does;
+    the numbers that decision is made from).  A trace is DIRECT when the seed
+    shares a hit with that decision.  It is ONE HOP when the seed instead
+    shares a hit with an oracle x-z candidate that itself shares a hit with
+    the decision: a candidate that exists on one side only (a window or cut
+    flip) changes the clone-killing vote of every seed it shares a hit with.
+    The two kinds are counted apart, and one-hop traces are bounded by
+    hop_max() (they excuse more than direct ones do);
   * for seeds in both sets the fitted quantities must agree within the
     tolerances of TOL (positions 1e-3 mm, slopes 1e-6; derived ones below).
 Matching is compared on identical seed states (the GPU's float32 states are
 the input of both sides): the chosen VELO index per seed must be equal unless
-a matching ledger entry of that seed is within TAU.
+a matching ledger entry within TAU names that seed and the VELO segment one of
+the two sides chose (a preselection or chi2 cut of that pair, or the argmin
+tie between the two).
 """
 
 from __future__ import annotations
@@ -32,6 +39,12 @@ AGREE_MIN = 0.999
 TOL = {"a": 1e-3, "b": 1e-6, "c": 1e-9, "y0": 1.1e-2, "ty": 1e-6,
        "x_s": 1e-3, "y_s": 1e-3, "tx_s": 1e-6, "ty_s": 1e-6}
 CHI2_REL = 1e-4
+
+
+def hop_max(n_union):
+    """Largest number of one-hop traces a comparison may contain: 2, or 2e-4
+    of the compared seeds (a fifth of the disagreement AGREE_MIN allows)."""
+    return max(2, int(2e-4 * n_union))
 
 
 def config_pair(zmx=None, **overrides):
@@ -55,9 +68,15 @@ class Report:
     n_common: int = 0
     untraced: List[tuple] = field(default_factory=list)
     traced: int = 0
+    traced_hop: int = 0          # of `traced`: through an oracle candidate
+    traced_kinds: Dict[str, int] = field(default_factory=dict)  # direct traces by decision kind
     max_err: Dict[str, float] = field(default_factory=dict)
     bad_params: List[tuple] = field(default_factory=list)
     chi2_rel: float = 0.0
+
+    @property
+    def n_union(self):
+        return self.n_gpu + self.n_cpu - self.n_common
 
     @property
     def agreement(self):
@@ -70,6 +89,9 @@ class Report:
         self.n_common += o.n_common
         self.untraced += o.untraced
         self.traced += o.traced
+        self.traced_hop += o.traced_hop
+        for k, v in o.traced_kinds.items():
+            self.traced_kinds[k] = self.traced_kinds.get(k, 0) + v
         self.bad_params += o.bad_params
         for k, v in o.max_err.items():
             self.max_err[k] = max(self.max_err.get(k, 0.0), v)
@@ -77,7 +99,8 @@ class Report:
 
     def summary(self):
         return (f"gpu={self.n_gpu} cpu={self.n_cpu} common={self.n_common} agree={self.agreement:.6f} "
-                f"traced={self.traced} untraced={len(self.untraced)} bad_params={len(self.bad_params)} "
+                f"traced={self.traced} (one hop {self.traced_hop}, direct by kind {self.traced_kinds}) "
+                f"untraced={len(self.untraced)} bad_params={len(self.bad_params)} "
                 f"chi2_rel={self.chi2_rel:.2e} max_err={ {k: float(f'{v:.3g}') for k, v in self.max_err.items()} }")
 
 
@@ -101,8 +124,16 @@ def compare_seeding_event(e, gpu: Dict[str, np.ndarray], ref: Dict[str, object],
             if hs & near_hits:
                 ext |= hs
         for t in diff:
-            if {h for h in t if h >= 0} & ext:
+            hs = {h for h in t if h >= 0}
+            if hs & near_hits:
                 r.traced += 1
+                kinds = {oracle.LEDGER_KINDS.get(int(n["kind"]), str(int(n["kind"]))) for n in near
+                         if hs & {int(h) for h in n["hits"] if h >= 0}}
+                for k in kinds:
+                    r.traced_kinds[k] = r.traced_kinds.get(k, 0) + 1
+            elif hs & ext:
+                r.traced += 1
+                r.traced_hop += 1
             else:
                 r.untraced.append((e, t, "gpu" if t in G else "oracle"))
     for t in common:
@@ -125,6 +156,15 @@ def compare_seeding_event(e, gpu: Dict[str, np.ndarray], ref: Dict[str, object],
         if int(gpu["n_hits"][gi][0]) != int(s["nx"]) or int(gpu["n_hits"][gi][1]) != int(s["nuv"]):
             r.bad_params.append((e, t, "n_hits", tuple(gpu["n_hits"][gi]), (s["nx"], s["nuv"])))
     return r
+
+
+def assert_seeding(rep: Report):
+    """The seeding acceptance rules on a comparison report."""
+    assert rep.agreement >= AGREE_MIN, rep.summary()
+    assert not rep.untraced, (rep.summary(), rep.untraced[:5])
+    assert rep.traced_hop <= hop_max(rep.n_union), rep.summary()
+    assert not rep.bad_params, (rep.summary(), rep.bad_params[:5])
+    assert rep.chi2_rel <= CHI2_REL, rep.summary()
 
 
 def oracle_seeding(ocfg, batch, events, tau_record=1e-4, threads=None):
@@ -154,9 +194,10 @@ def compare_matching(gpu, ocfg, batch, events=None, tau=TAU):
         gv = gpu["velo_idx"][s0:s1]
         n += s1 - s0
         led = m["ledger"]
-        near = set(int(s) for s in led[led["margin"] <= tau]["hits"][:, 0]) if len(led) else set()
+        near = led[led["margin"] <= tau] if len(led) else led
         for k in np.nonzero(gv != m["velo_idx"])[0]:
-            if k in near:
+            pair = {int(gv[k]), int(m["velo_idx"][k])} - {-1}
+            if any(int(n["hits"][0]) == k and pair & {int(n["hits"][1]), int(n["hits"][2])} for n in near):
                 traced += 1
             else:
                 untraced.append((e, int(k), int(gv[k]), int(m["velo_idx"][k])))

@@ -127,7 +127,7 @@ def test_fused_full_size_run3_against_oracle(zmx):
     rng = np.random.default_rng(21)
     ev = np.sort(rng.choice(b.n_events, 40, replace=False))
     rep = parity.compare_seeding(got, ocfg, b, ev)
-    assert rep.agreement >= parity.AGREE_MIN and not rep.untraced and not rep.bad_params, rep.summary()
+    parity.assert_seeding(rep)
     _, untraced, _, _ = parity.compare_matching(got, ocfg, b, ev)
     assert not untraced, untraced[:5]
 

@@ -40,10 +40,7 @@ def run_gpu(batch, gcfg, cap=None, **kw):
 
 
 def assert_seeding_parity(rep: parity.Report):
-    assert rep.agreement >= parity.AGREE_MIN, rep.summary()
-    assert not rep.untraced, (rep.summary(), rep.untraced[:5])
-    assert not rep.bad_params, (rep.summary(), rep.bad_params[:5])
-    assert rep.chi2_rel <= parity.CHI2_REL, rep.summary()
+    parity.assert_seeding(rep)
 
 
 @pytest.mark.parametrize("name,n", [("tiny", None), ("run3", 200), ("match_stress", 40), ("uneven", 200)])

@@ -2,8 +2,12 @@
 
 A copy of oracle.c is edited in a temporary directory (one mistake per copy:
 a dropped term, a wrong sign, a transposed operand, a wrong index), compiled,
-and the pin checks of test_oracle_pins.py are run against it.  At least one
-check must fail for every mutant.  The real oracle is never modified.
+and the pin checks of test_oracle_pins.py and test_ledger_pins.py are run
+against it.  At least one check must fail for every mutant.  The real oracle
+is never modified.  The "ledger_*" mutants plant mistakes in the cut ledger
+(a margin left unnormalised or measured to the wrong edge, the wrong hits
+named, entries dropped): the ledger decides which GPU/oracle differences are
+excused, so a mistake there must not pass unseen.
 """
 
 import os
@@ -11,6 +15,7 @@ import os
 import pytest
 
 import oracle
+import test_ledger_pins as ledger_pins
 import test_oracle_pins as pins
 
 MUTATIONS = {
@@ -59,6 +64,31 @@ MUTATIONS = {
     "pmin_iter_ignored": ("return it >= 0 && it < 3 && c->p_min_iter[it] > 0 ? c->p_min_iter[it] : c->p_min;",
                           "return c->p_min;"),
     "used_t3_ignored": ("                if (E->used && E->used[h3]) continue;\n", ""),
+    "ledger_pair_unscaled": ("double m = fmin(fabs(x3 - lo), fabs(x3 - hi)) / dmax2(S3, fabs(x3));",
+                             "double m = fmin(fabs(x3 - lo), fabs(x3 - hi));"),
+    "ledger_pair_far_edge": ("double m = fmin(fabs(x3 - lo), fabs(x3 - hi)) / dmax2(S3, fabs(x3));",
+                             "double m = fmax(fabs(x3 - lo), fabs(x3 - hi)) / dmax2(S3, fabs(x3));"),
+    "ledger_trip_unscaled": ("double m = fmin(fabs(x2 - lo2), fabs(x2 - hi2)) / dmax2(S2, fabs(x2));",
+                             "double m = fmin(fabs(x2 - lo2), fabs(x2 - hi2));"),
+    "ledger_trip_hit_order": ("int32_t hh[3] = {h1, h3, h2};", "int32_t hh[3] = {h1, h2, h3};"),
+    "ledger_tol_unscaled": ("ledger_add(E, kind_tol, half, fabs(d - tol) / S, hh, nh + 1);",
+                            "ledger_add(E, kind_tol, half, fabs(d - tol), hh, nh + 1);"),
+    "ledger_tol_wrong_hit": ("hh[nh] = E->zl[zi][k].i;", "hh[nh] = -1;"),
+    "ledger_tie_unscaled": ("fabs(second - bestd) / dmax2(scale, 1.0)", "fabs(second - bestd)"),
+    "ledger_chi2_unnormalised": ("fabs(q - c->chi2x_max) / c->chi2x_max", "fabs(q - c->chi2x_max)"),
+    "ledger_clone_absolute": ("double m = fabs(a->score - w->score) / dmax2(a->score, w->score);",
+                              "double m = fabs(a->score - w->score);"),
+    "ledger_clone_wrong_hits": ("hh[6 + q] = w->hits[q];", "hh[6 + q] = a->hits[q];"),
+    "ledger_uv_win_in_y": ("double m = fmin(fabs(y - ylo), fabs(y - yhi)) * fabs(tI) /",
+                           "double m = fmin(fabs(y - ylo), fabs(y - yhi)) /"),
+    "ledger_uv_sel_absolute": (
+        "double m = fabs(all[k].chi2 - all[b].chi2) / dmax2(dmax2(all[k].chi2, all[b].chi2), 1e-300);",
+        "double m = fabs(all[k].chi2 - all[b].chi2);"),
+    "ledger_presel_absolute": ("fabs(val[q] - cut[q]) / cut[q]", "fabs(val[q] - cut[q])"),
+    "ledger_m_chi2_absolute": ("fabs(chi2 - c->chi2_match_max) / c->chi2_match_max",
+                               "fabs(chi2 - c->chi2_match_max)"),
+    "ledger_m_tie_absolute": ("fabs(schi - bchi) / dmax2(schi, 1e-300)", "fabs(schi - bchi)"),
+    "ledger_drops_entries": ("if (!(margin <= E->tau)) return;", "if (!(margin <= 0.01 * E->tau)) return;"),
     "state_slope": ("s->tx_s = cd->th[1] + cd->th[2] * (2.0 * zb + 3.0 * c->d_ratio * zb * zb);",
                     "s->tx_s = cd->th[1];"),
 }
@@ -74,7 +104,7 @@ def test_pins_catch_planted_mistake(name, tmp_path, zmx_calibrated):
     so = oracle.build(force=True, src=str(mpath), out=str(tmp_path / "liboracle_mut.so"))
     L = oracle.lib(so)
     failed = []
-    for chk in pins.ALL_CHECKS:
+    for chk in pins.ALL_CHECKS + ledger_pins.ALL_CHECKS:
         kw = {"zmx": zmx_calibrated} if chk is pins.check_noise_free_recovery else {}
         try:
             chk(L, **kw)
