@@ -55,8 +55,15 @@ N_SMS = 152
 FP32_LANES_PER_SM = 128
 
 # Per-unit FP32 operation costs of the seeding and matching steps (the
-# algorithmic work model; units are counted by the kernels themselves).
-OPS_PER_UNIT = {"pairs": 12.0, "triplets": 40.0, "fits": 120.0, "uv_init": 60.0, "match_pairs": 45.0}
+# algorithmic work model; units are counted by the kernels themselves).  An
+# operation is one FP32 / integer instruction per lane (a fused multiply-add
+# counts once), so the peak is one operation per lane per cycle.  The
+# extension of a triplet searches the 3 other x-layers for the closest hit
+# (a binary search over the layer's hits plus a few compares per layer);
+# matching pairs are those the kernel evaluates (in the ty buckets the |dty|
+# preselection can reach), not the full VELO x seed grid.
+OPS_PER_UNIT = {"pairs": 12.0, "triplets": 40.0, "fits": 120.0, "uv_init": 60.0, "match_eval": 45.0}
+EXT_OPS_BASE = 6.0  # per searched layer, on top of log2(hits per zone)
 
 
 def log(*a):
@@ -161,13 +168,14 @@ def traffic_from_profile(kernel):
 # oracle (CPU) timing
 # ---------------------------------------------------------------------------
 
-def time_oracle(batch, zmx, budget_s=12.0, events=None, cores=None):
+def time_oracle(batch, zmx, budget_s=12.0, events=None, cores=None, windows=None):
     """Seeding + matching of events by the FP64 oracle on `cores` host
     threads (all by default), one event per task; stops after the budget.
+    windows: the window-width overrides the GPU arm runs with.
     Returns (events/s, cores, n)."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
-    cfg = oracle.default_config(zmx=zmx)
+    cfg = oracle.default_config(zmx=zmx, **(windows or {}))
     cores = cores or os.cpu_count() or 1
     events = list(range(batch.n_events)) if events is None else list(events)
 
@@ -191,6 +199,15 @@ def time_oracle(batch, zmx, budget_s=12.0, events=None, cores=None):
     return done / dt, cores, done
 
 
+def applied_windows(args):
+    """The window widths both arms run with: the autotuner's committed pick,
+    or the paper's widths with --no-autotune / --paper-windows."""
+    if args.no_autotune or args.paper_windows:
+        return {}
+    from paper_2606_14480_gb300 import autotune
+    return autotune.tuned_windows()
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if ws > 1 and rank != 0:
@@ -198,11 +215,12 @@ def run_reference(args):
     from synth import calibrate_zmatch, make_workload
     batch = make_workload(WORKLOAD)
     zmx = calibrate_zmatch(7826.0)
+    windows = applied_windows(args)
     vals = []
     n_total = 0
     for k in range(args.warmup + args.steps):
         budget = 1.0 if k < args.warmup else max(2.0, min(10.0, 60.0 / max(1, args.steps)))
-        v, cores, n = time_oracle(batch, zmx, budget_s=budget)
+        v, cores, n = time_oracle(batch, zmx, budget_s=budget, windows=windows)
         if k >= args.warmup:
             vals.append(v)
             n_total += n
@@ -211,7 +229,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 1000 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"{WORKLOAD}: 1000 events, Poisson(150) tracks, 30% noise",
-                                            "events_per_step": 1000, "l2": "n/a (CPU)"},
+                                            "events_per_step": 1000, "l2": "n/a (CPU)", "windows": windows},
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
                              "sample": f"{n_total} events of the workload, one event per task on {cores} threads"},
             "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -237,6 +255,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="batched measurement only (for profiling)")
     ap.add_argument("--no-autotune", action="store_true", help="paper defaults, no launch-shape tuning")
+    ap.add_argument("--paper-windows", action="store_true", help="the paper's window widths, not the tuned ones")
     ap.add_argument("--no-variants", action="store_true", help="skip the Hough-cluster UV measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -264,25 +283,35 @@ def main():
     # tuner keeps the GPU busy, so the samples are taken under load)
     clocks = ClockSampler(local).start()
     tuned, tune_report = {}, None
+    windows = applied_windows(args)
     if not args.no_autotune:
         from paper_2606_14480_gb300 import autotune
         t0 = time.perf_counter()
         calib = autotune.calibration_from_synth(batch)
         tb = autotune._Bench(calib, local, reps=5, flush_mb=256)
-        lr = autotune.tune_launch({"zmx": zmx}, bench=tb)
+        lr = autotune.tune_launch(dict({"zmx": zmx}, **windows), bench=tb)
         tuned = dict(lr.best)
         tune_report = {"launch": lr.report(), "applied": tuned}
+        rec = autotune.tuned_windows_record()
+        tune_report["windows"] = {"applied": bool(windows), "values": windows,
+                                  "source": "tuned_windows.json (window sweep on a GB300, calibration batch "
+                                            + (rec or {}).get("calibration", "?") + ")",
+                                  "tuned_eff": (rec or {}).get("eff"), "tuned_ghost": (rec or {}).get("ghost"),
+                                  "paper_eff": ((rec or {}).get("paper_widths") or {}).get("eff"),
+                                  "paper_ghost": ((rec or {}).get("paper_widths") or {}).get("ghost")}
         if not args.quick:
+            # the sweep again, on this batch: does it pick the same point?
             wr = autotune.tune_windows(dict({"zmx": zmx}, **tuned), bench=tb)
-            tune_report["windows"] = wr.report()
-            tune_report["windows"]["grid"] = [
+            tune_report["windows"]["rerun"] = wr.report()
+            tune_report["windows"]["rerun"]["agrees"] = all(
+                abs(float(wr.best.get(k, 0.0)) - float(v)) < 1e-12 for k, v in windows.items())
+            tune_report["windows"]["rerun"]["grid"] = [
                 {"overrides": q.overrides, "ms": q.ms, "eff": q.eff, "ghost": q.ghost, "ok": q.ok}
                 for q in wr.points]
-            tune_report["windows"]["applied"] = False
         del tb
         tune_report["seconds"] = time.perf_counter() - t0
         log(f"autotune: {tune_report}")
-    cfg = st.st_config_default(zmx=zmx, **tuned)
+    cfg = st.st_config_default(zmx=zmx, **windows, **tuned)
     ctx = st.Context(cfg, device=local)
     db = st.DeviceBatch.from_synth(batch, device=dev)
     cap = max(1024, batch.n_hits // 4)
@@ -333,10 +362,15 @@ def main():
               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32",
               "data": "synthetic (seeded generator; Run-3-like occupancy)",
-              "config": {"workload": f"{WORKLOAD}: 1000 events, Poisson(150) tracks/event, 30% noise hits, "
-                                     f"{batch.n_hits / n_ev:.0f} hits/event, VELO truth + 20% ghosts",
+              "config": {"workload": f"Run-3-like batch ({WORKLOAD}): 1000 events, Poisson(150) tracks/event, "
+                                     f"30% noise hits, {batch.n_hits / n_ev:.0f} hits/event, VELO truth + 20% "
+                                     f"ghosts",
+                         "headline": "the Run-3-like 1000-event batch is the configuration the metric is quoted "
+                                     "on; the 10 000-event uneven-occupancy batch in one graph launch is "
+                                     "uneven_batched",
                          "events_per_step": n_ev, "mode": "batched: one CUDA graph of persistent kernels",
                          "l2": "flushed between steps (256 MB write, untimed)",
+                         "windows": windows or "the paper's widths",
                          "seeds_per_event": counters["seeds"] / max(1, counters["events"])},
               "gpu_launches": kernels_per_step * args.steps}
     if clk:
@@ -350,20 +384,23 @@ def main():
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     steps = args.steps
     seed_ms = kms["seed"] / steps
-    units = {k: counters[k] / steps for k in ("pairs", "triplets", "ext_ok", "uv_init", "match_pairs")}
-    ops = (OPS_PER_UNIT["pairs"] * units["pairs"] + OPS_PER_UNIT["triplets"] * units["triplets"]
+    units = {k: counters[k] / steps for k in ("pairs", "triplets", "ext_ok", "uv_init", "match_eval")}
+    ext_ops = 3.0 * (math.log2(max(2.0, batch.n_hits / (24.0 * n_ev))) + EXT_OPS_BASE)
+    ops = (OPS_PER_UNIT["pairs"] * units["pairs"] + (OPS_PER_UNIT["triplets"] + ext_ops) * units["triplets"]
            + OPS_PER_UNIT["fits"] * units["ext_ok"] + OPS_PER_UNIT["uv_init"] * units["uv_init"])
     if fused:  # the seeding kernel also matches every seed against its event's VELO segments
-        ops += OPS_PER_UNIT["match_pairs"] * units["match_pairs"]
-    peak_tflops = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        ops += OPS_PER_UNIT["match_eval"] * units["match_eval"]
+    peak_tops = N_SMS * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     achieved = ops / (seed_ms / 1000.0) / 1e12 if seed_ms > 0 else 0.0
     traffic = traffic_from_profile("k_seed")
-    result["roofline"] = {"kernel": "k_seed (matching fused in)" if fused else "k_seed", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                          "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                          "peak_source": f"FP32: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
-                                         f"({src} sm_max_mhz)",
+    result["roofline"] = {"kernel": "k_seed (matching fused in)" if fused else "k_seed", "bound": "alu",
+                          "achieved": achieved, "peak": peak_tops, "unit": "Tops/s", "frac": achieved / peak_tops,
+                          "traffic": traffic,
+                          "peak_source": f"FP32 lanes: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 1 op x "
+                                         f"{sm_mhz:.0f} MHz ({src} sm_max_mhz)",
+                          "ops_per_unit": dict(OPS_PER_UNIT, extension_per_triplet=ext_ops),
                           "kernel_ms": {k: v / steps for k, v in kms.items()},
-                          "units_per_launch": units,
+                          "units_per_launch": dict(units, grid_pairs=counters["match_pairs"] / steps),
                           "hbm": {"algorithmic_bytes": None, "peak_gbs": float(peaks.get("hbm_gbs", 6800.0))}}
     # algorithmic HBM bytes of one seeding launch: containers (x, original
     # index) read once, seed records (48 + 32 + 16 + 2 B) written once; fused,
@@ -372,7 +409,10 @@ def main():
     if fused:
         alg_bytes += 16.0 * batch.velo.shape[0] + 8.0 * counters["seeds"] / steps
     result["roofline"]["hbm"]["algorithmic_bytes"] = alg_bytes
-    result["roofline"]["hbm"]["achieved_gbs"] = alg_bytes / (seed_ms / 1000.0) / 1e9 if seed_ms > 0 else 0.0
+    hbm_gbs = alg_bytes / (seed_ms / 1000.0) / 1e9 if seed_ms > 0 else 0.0
+    result["roofline"]["hbm"]["achieved_gbs"] = hbm_gbs
+    result["roofline"]["hbm"]["frac"] = hbm_gbs / float(peaks.get("hbm_gbs", 6800.0))
+    result["roofline"]["hbm"]["peak_source"] = f"{src} hbm_gbs"
     # instruction-issue view of the same launch: warp instructions (ncu, same
     # kernel source) over the live launch time against 4 issue slots per SM
     rec = profile_record("k_seed")
@@ -385,20 +425,28 @@ def main():
 
     # ---------------- the Hough-cluster UV variant on the same batch
     if not args.no_variants:
-        result["uv_hough"] = time_variant(st, dict(zmx=zmx, uv_mode=1, **tuned), db, out, cap, n_ev, flush,
+        result["uv_hough"] = time_variant(st, dict(zmx=zmx, uv_mode=1, **windows, **tuned), db, out, cap, n_ev, flush,
                                           stream, args.steps)
         log(f"uv_hough: {result['uv_hough']}")
         from synth import ghost_nn_weights
-        result["final_selection"] = time_variant(st, dict(zmx=zmx, final_sel=1, **tuned), db, out, cap, n_ev,
+        result["final_selection"] = time_variant(st, dict(zmx=zmx, final_sel=1, **windows, **tuned), db, out, cap, n_ev,
                                                  flush, stream, args.steps, nn=ghost_nn_weights())
         result["final_selection"]["weights"] = "seeded stand-in (the trained weights are not published)"
         log(f"final_selection: {result['final_selection']}")
         result["iterations_hlt2"] = time_variant(
-            st, dict(zmx=zmx, iter_mode=1, n_iter=3, p_min_iter=[5000.0, 3000.0, 1500.0], **tuned), db, out, cap,
+            st, dict(zmx=zmx, iter_mode=1, n_iter=3, p_min_iter=[5000.0, 3000.0, 1500.0], **windows, **tuned), db, out, cap,
             n_ev, flush, stream, args.steps)
         log(f"iterations_hlt2: {result['iterations_hlt2']}")
         result["uneven_batched"] = time_uneven(st, cfg, local, flush, stream, args.steps)
         log(f"uneven_batched: {result['uneven_batched']}")
+        result["match_stress"] = time_match_stress(st, dict(zmx=zmx, **windows, **tuned), local, flush, stream,
+                                                   args.steps)
+        log(f"match_stress: {result['match_stress']}")
+        if windows:
+            result["paper_widths"] = time_variant(st, dict(zmx=zmx, **tuned), db, out, cap, n_ev, flush, stream,
+                                                  args.steps)
+            result["paper_widths"]["config"]["windows"] = "the paper's widths (dx3_scale 1, m_lo 0.5, m_hi 1.5)"
+            log(f"paper_widths: {result['paper_widths']}")
         graph.st_graph_launch(stream)  # the default configuration's outputs again
         stream.synchronize()
         result["ut"] = time_ut(st, ctx, db, out, flush, stream, args.steps)
@@ -486,24 +534,31 @@ def main():
         per = np.array([a.elapsed_time(b) for a, b in zip(marks, marks[1:])])
         result["per_event"] = {"value": pe / (pe_ms / 1000.0), "unit": "events/s", "events_timed": pe,
                                "launches_per_event": 6,
-                               "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
-                               "mode": "seeding_run + matching_run per event, one stream (latency: between "
-                                       "consecutive events' completion on the stream)"}
+                               "completion_gap_p50_ms": float(np.percentile(per, 50)),
+                               "completion_gap_p99_ms": float(np.percentile(per, 99)),
+                               "mode": "seeding_run + matching_run per event, one stream, back to back (the gap "
+                                       "is between consecutive events' completion on the stream; submit-to-"
+                                       "result latency under Poisson arrivals is in served.equal_load)"}
         del C
         ctx3.close()
         log(f"per-event: {pe_ms / pe:.4f} ms/event")
 
         # ---------------- served: continuous batching of a Poisson request stream
-        result["served"] = serve(st, cfg, args, local)
+        result["served"] = serve(st, cfg, args, local, per_event_rate=result["per_event"]["value"])
         log(f"served: {result['served']}")
+        eq = result["served"].get("equal_load")
+        if eq:
+            result["per_event"]["p50_ms"] = eq["per_event_launch"]["p50_ms"]
+            result["per_event"]["p99_ms"] = eq["per_event_launch"]["p99_ms"]
+            result["per_event"]["latency"] = "submit to result under Poisson arrivals (served.equal_load)"
 
         # ---------------- CPU baseline: the oracle on the host cores
         if not args.no_cpu_baseline:
-            v, cores, n = time_oracle(batch, zmx, budget_s=10.0)
-            v1, _, n1 = time_oracle(batch, zmx, budget_s=4.0, cores=1)
+            v, cores, n = time_oracle(batch, zmx, budget_s=10.0, windows=windows)
+            v1, _, n1 = time_oracle(batch, zmx, budget_s=4.0, cores=1, windows=windows)
             unev = make_workload("uneven", n_events=2000, seed=1003)
-            vu, _, nu = time_oracle(unev, zmx, budget_s=6.0)
-            vu1, _, nu1 = time_oracle(unev, zmx, budget_s=4.0, cores=1)
+            vu, _, nu = time_oracle(unev, zmx, budget_s=6.0, windows=windows)
+            vu1, _, nu1 = time_oracle(unev, zmx, budget_s=4.0, cores=1, windows=windows)
             result["cpu_baseline"] = {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
                                       "sample": f"{n} events of the workload (cycled), seeding + matching, "
                                                 f"FP64, one event per task on {cores} threads, ~10 s",
@@ -647,12 +702,108 @@ def poll_grow(st, ctx, ticket, n_events, timeout_us=60_000_000):
         return info
 
 
-def serve(st, cfg, args, local):
+class _Collector(threading.Thread):
+    """Polls outstanding tickets in completion order: each sweep polls (without
+    waiting) the oldest K pending tickets, so a small request that completes
+    behind a large one is collected at once rather than after it.  Latency =
+    pipeline_poll's return - pipeline_submit's entry (st_request_info)."""
+
+    K = 32
+
+    def __init__(self, st, ctx, tickets, lat, buf):
+        super().__init__(daemon=True)
+        self.st, self.ctx, self.tickets, self.lat, self.buf = st, ctx, tickets, lat, buf
+        self.errors = []
+
+    def run(self):
+        st, n = self.st, len(self.tickets)
+        pending, nxt, done = [], 0, 0
+        try:
+            while done < n:
+                while nxt < n and self.tickets[nxt] is not None:
+                    pending.append(nxt)
+                    nxt += 1
+                got = False
+                for i in list(pending[: self.K]):
+                    rc, info = self.ctx.pipeline_poll(self.tickets[i], self.buf.seeds, self.buf.long, 0)
+                    if rc == st.ST_OK:
+                        self.lat[i] = (info.t_returned_ns - info.t_submit_ns) / 1e6
+                        pending.remove(i)
+                        done += 1
+                        got = True
+                    elif rc != st.ST_PENDING:
+                        raise RuntimeError(f"pipeline_poll: {st.STATUS_NAMES.get(rc, rc)}")
+                if not got:
+                    if self.errors:
+                        return
+                    time.sleep(0.00005)
+        except Exception as exc:  # surfaced by the main thread
+            self.errors.append(exc)
+
+
+def _serve_stream(st, ctx, pool_arrays, sizes, arr, starts, big, timeout_s):
+    """Submit requests at their arrival times from this thread while a
+    collector thread polls; returns (latencies ms, wall s)."""
+    ev_off, x, zone, velo_off, velo, mh = pool_arrays
+    n_req = len(sizes)
+    lat = [None] * n_req
+    tickets = [None] * n_req
+    col = _Collector(st, ctx, tickets, lat, big)
+    col.start()
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        wait = arr[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        s0, n = starts[i], int(sizes[i])
+        hits = st.StHits(n, ev_off[s0:].ctypes.data, x.ctypes.data, zone.ctypes.data, None, None, mh, 0)
+        vel = st.StVelo(n, velo_off[s0:].ctypes.data, velo.ctypes.data)
+        tickets[i] = ctx.pipeline_submit(hits, vel)
+    col.join(timeout=timeout_s)
+    if col.is_alive():
+        col.errors.append(RuntimeError("served requests did not complete in time"))
+    if col.errors:
+        raise col.errors[0]
+    return np.array(lat, dtype=np.float64), time.perf_counter() - t0
+
+
+def _per_event_stream(st, ctx, db, outs, sizes, arr, starts, stream):
+    """The plain per-event launch as a server: requests handled first come,
+    first served by one worker; each event of a request is seeding_run +
+    matching_run on one stream (inputs resident on the device, which favours
+    this path), and a request is done when its stream work has finished.
+    Latency = done - arrival."""
+    import torch
+    n_req = len(sizes)
+    lat = np.zeros(n_req)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(n_req):
+            wait = arr[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            for e in range(starts[i], starts[i] + int(sizes[i])):
+                h = st.StHits(1, db.ev_off.data_ptr() + 8 * e, db.x.data_ptr(), db.zone.data_ptr(), None, None,
+                              db.max_hits, 0)
+                v = st.StVelo(1, db.velo_off.data_ptr() + 8 * e, db.velo.data_ptr())
+                ctx.seeding_run(h, outs.seeds, stream)
+                ctx.matching_run(v, outs.seeds, outs.long, stream)
+            stream.synchronize()
+            lat[i] = (time.perf_counter() - t0 - arr[i]) * 1000.0
+    return lat, time.perf_counter() - t0
+
+
+def serve(st, cfg, args, local, per_event_rate=None):
     """Continuous batching of a Poisson request stream.  Requests carry
     log-uniform 1-4096 events, each a contiguous window of a pool of events
     with log-normal occupancy (passed to pipeline_submit without a copy).
     Offered rates are fractions of the batched capacity measured on the same
-    pool; latency = pipeline_poll return - pipeline_submit entry."""
+    pool.  Before the first rate the pipeline serves a few requests of every
+    size decade (first-use costs stay out of the numbers).  With
+    per_event_rate (events/s the plain per-event launch sustains), the same
+    Poisson arrivals at half that rate, with smaller requests (log-uniform
+    1-256 events), go once through the pipeline and once through per-event
+    launches: submit-to-result latency of both at equal load."""
     import torch
     from synth import make_workload
     from synth.events import poisson_arrivals, serving_requests
@@ -663,9 +814,11 @@ def serve(st, cfg, args, local):
     zone = np.ascontiguousarray(pool.zone, np.int32)
     velo = np.ascontiguousarray(pool.velo, np.float32)
     mh = int(np.max(np.diff(ev_off)))
+    arrays = (ev_off, x, zone, velo_off, velo, mh)
+    dev = torch.device("cuda", local)
     # batched capacity on this pool (graph replay, inputs resident)
     ctx0 = st.Context(cfg, device=local)
-    db = st.DeviceBatch.from_synth(pool, device=torch.device("cuda", local))
+    db = st.DeviceBatch.from_synth(pool, device=dev)
     cap = max(1024, pool.n_hits // 4)
     out0 = st.DeviceOutputs(pool.n_events, cap, device=db.x.device)
     ctx0.st_reserve(pool.n_events, pool.n_events * db.max_hits, db.max_hits, cap)
@@ -682,14 +835,20 @@ def serve(st, cfg, args, local):
     capacity = 5 * pool.n_events / (e0.elapsed_time(e1) / 1000.0)
     g.close()
     ctx0.close()
-    del db, out0
+    del out0
 
     ctx = st.Context(cfg, device=local)
     ctx.st_pipeline_configure(n_slots=4, max_events_per_slot=4096, max_hits_per_slot=4096 * 4000,
                               max_hits_per_event=mh, max_velo_per_event=4096, max_velo_per_slot=4096 * 1024)
-    big = st.HostBuffers(4096, 4096 * 300 + 1024)  # reused by the poller
-    out = {"capacity_events_per_s": capacity, "pool": "8192 events, log-normal occupancy (median 120 tracks)"}
+    big = st.HostBuffers(4096, 4096 * 300 + 1024)  # reused by the collector
+    out = {"capacity_events_per_s": capacity, "pool": "8192 events, log-normal occupancy (median 120 tracks)",
+           "latency": "pipeline_poll return - pipeline_submit entry; tickets polled in completion order",
+           "warmup": "two requests of 1, 10, 100, 1000 and 4096 events before the first rate"}
     rng = np.random.default_rng(1007)
+    # warm-up: every size decade, so that first-use costs are not measured
+    wsz = np.array([1, 1, 10, 10, 100, 100, 1000, 1000, 4096, 4096])
+    _serve_stream(st, ctx, arrays, wsz, np.zeros(len(wsz)), [int(rng.integers(0, pool.n_events - n + 1)) for n in wsz],
+                  big, 120.0)
     for frac in [float(f) for f in args.serve_rates.split(",") if f]:
         rate = frac * capacity  # events/s offered
         n_events_total = int(min(rate * args.serve_seconds, args.serve_events))
@@ -697,54 +856,83 @@ def serve(st, cfg, args, local):
         n_req = len(sizes)
         arr = poisson_arrivals(n_req, rate / float(np.mean(sizes)), seed=1006)
         starts = [int(rng.integers(0, pool.n_events - n + 1)) for n in sizes]
-        lat = [None] * n_req
-        tickets = [None] * n_req
-        done = threading.Event()
-        errors = []
-
-        def poller():
-            try:
-                for i in range(n_req):
-                    while tickets[i] is None:
-                        if errors:
-                            return
-                        time.sleep(0.0001)
-                    rc, info = ctx.pipeline_poll(tickets[i], big.seeds, big.long, 60_000_000)
-                    if rc != st.ST_OK:
-                        raise RuntimeError(f"pipeline_poll: {st.STATUS_NAMES.get(rc, rc)}")
-                    lat[i] = (info.t_returned_ns - info.t_submit_ns) / 1e6
-            except Exception as exc:  # surfaced by the main thread
-                errors.append(exc)
-            finally:
-                done.set()
-
-        th = threading.Thread(target=poller, daemon=True)
-        th.start()
-        t0 = time.perf_counter()
-        for i in range(n_req):
-            wait = arr[i] - (time.perf_counter() - t0)
-            if wait > 0:
-                time.sleep(wait)
-            s0, n = starts[i], int(sizes[i])
-            hits = st.StHits(n, ev_off[s0:].ctypes.data, x.ctypes.data, zone.ctypes.data, None, None, mh, 0)
-            vel = st.StVelo(n, velo_off[s0:].ctypes.data, velo.ctypes.data)
-            try:
-                tickets[i] = ctx.pipeline_submit(hits, vel)
-            except Exception as exc:
-                errors.append(exc)
-                break
-        if not done.wait(timeout=120.0 + 20.0 * args.serve_seconds):
-            raise RuntimeError("served requests did not complete in time")
-        if errors:
-            raise errors[0]
-        wall = time.perf_counter() - t0
-        lat_a = np.array(lat)
+        lat_a, wall = _serve_stream(st, ctx, arrays, sizes, arr, starts, big, 120.0 + 20.0 * args.serve_seconds)
         out[f"{frac:g}"] = {"offered_events_per_s": rate, "events_per_s": float(np.sum(sizes) / wall),
                             "requests": n_req, "events": int(np.sum(sizes)), "wall_s": wall,
                             "p50_ms": float(np.percentile(lat_a, 50)), "p99_ms": float(np.percentile(lat_a, 99))}
         log(f"served {frac:g}: {out[f'{frac:g}']}")
+
+    if per_event_rate:
+        # equal load: the same arrivals through both paths
+        rate = 0.5 * per_event_rate
+        sizes = serving_requests(int(rate * 4.0), seed=1008, batch_hi=256)
+        arr = poisson_arrivals(len(sizes), rate / float(np.mean(sizes)), seed=1009)
+        starts = [int(rng.integers(0, pool.n_events - n + 1)) for n in sizes]
+        lat_s, wall_s = _serve_stream(st, ctx, arrays, sizes, arr, starts, big, 120.0)
+        ctxp = st.Context(cfg, device=local)
+        ctxp.st_reserve(1, db.max_hits, db.max_hits, 8192)
+        outs = st.DeviceOutputs(1, 8192, device=dev)
+        stream = torch.cuda.Stream(device=dev)
+        _per_event_stream(st, ctxp, db, outs, sizes[:3], np.zeros(3), starts[:3], stream)  # warm-up
+        lat_p, wall_p = _per_event_stream(st, ctxp, db, outs, sizes, arr, starts, stream)
+        ctxp.close()
+        out["equal_load"] = {
+            "offered_events_per_s": rate, "requests": len(sizes), "events": int(np.sum(sizes)),
+            "sizes": "log-uniform 1-256 events per request, Poisson arrivals",
+            "served": {"p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
+                       "events_per_s": float(np.sum(sizes) / wall_s)},
+            "per_event_launch": {"p50_ms": float(np.percentile(lat_p, 50)), "p99_ms": float(np.percentile(lat_p, 99)),
+                                 "events_per_s": float(np.sum(sizes) / wall_p),
+                                 "mode": "seeding_run + matching_run per event, requests first come first "
+                                         "served, inputs resident on the device"}}
+        log(f"equal load: {out['equal_load']}")
     ctx.close()
     return out
+
+
+def time_match_stress(st, overrides, local, flush, stream, steps):
+    """The matching-stress batch (2000 events; 280 tracks and 120 ghost VELO
+    segments, so 400 VELO segments per event; 40% noise hits): the seeds come
+    from one untimed seeding_run, then matching_run (k_match alone) is timed
+    per call, with the preselection cuts at 0.5x, 1x and 2x (the sweep widens
+    the ty buckets each seed visits)."""
+    import torch
+    from synth import make_workload
+    b = make_workload("match_stress")
+    dev = torch.device("cuda", local)
+    db = st.DeviceBatch.from_synth(b, device=dev)
+    cap = max(1024, b.n_hits // 4)
+    out = st.DeviceOutputs(b.n_events, cap, device=dev)
+    res = {"events": b.n_events, "velo_per_event": float(b.velo.shape[0]) / b.n_events,
+           "hits_per_event": b.n_hits / b.n_events}
+    for sc in (0.5, 1.0, 2.0):
+        ctx = st.Context(st.st_config_default(**dict(overrides, presel_scale=sc)), device=local)
+        ctx.st_reserve(b.n_events, b.n_events * db.max_hits, db.max_hits, cap)
+        with torch.cuda.stream(stream):
+            ctx.seeding_run(db.hits, out.seeds, stream)
+            for _ in range(3):
+                ctx.matching_run(db.velo_s, out.seeds, out.long, stream)
+            stream.synchronize()
+            ctx.st_read_counters(reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tot = 0.0
+            for _ in range(steps):
+                flush.fill_(1)
+                e0.record(stream)
+                ctx.matching_run(db.velo_s, out.seeds, out.long, stream)
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+        c = ctx.st_read_counters(reset=True)
+        seeds = int(out.ev_off[-1].item())
+        ms = tot / steps
+        res[f"presel_x{sc:g}"] = {"ms_per_call": ms, "events_per_s": b.n_events / (ms / 1000.0),
+                                  "seeds_per_event": seeds / b.n_events,
+                                  "grid_pairs_per_call": c["match_pairs"] / steps,
+                                  "evaluated_pairs_per_call": c["match_eval"] / steps,
+                                  "long_tracks_per_event": c["matched"] / steps / b.n_events}
+        ctx.close()
+    return res
 
 
 if __name__ == "__main__":

@@ -186,11 +186,15 @@ typedef struct {
     float* ghost_prob;
 } st_long;
 
-/* Per-stage work counters, summed over the calls since the last reset. */
+/* Per-stage work counters, summed over the calls since the last reset.
+ * match_pairs is the full VELO x seed grid of Section 4.2; match_eval the
+ * pairs the matching kernel actually evaluates (those in the ty buckets the
+ * |dty| preselection cut can reach; every other pair fails that cut). */
 typedef struct {
     int64_t pairs, triplets, ext_ok, cands, kept, uv_init, uv_cands, seeds;
     int64_t match_pairs, match_presel, matched;
     int64_t hits, events;
+    int64_t match_eval;
 } st_counters;
 
 typedef struct st_ctx st_ctx;
@@ -321,6 +325,18 @@ void st_graph_destroy(st_graph* graph);
 int st_set_timing(st_ctx* ctx, int enable);
 int st_kernel_ms(st_ctx* ctx, float ms[4]);
 
+/* Longest time (nanoseconds of the device's global timer) a CTA of the fused
+ * seeding kernel (st_graph_create, the serving pipeline) waits for an event
+ * that another running CTA is still seeding.  Default 200 ms; a correct run
+ * waits for microseconds.  A wait that runs out sets a fault word and every
+ * event of that launch gets status ST_TIMEOUT; the kernel returns normally
+ * and the context stays usable.  0 makes every such wait give up at once (to
+ * exercise that path).  Applies to launches prepared after the call (a graph
+ * keeps the limit it was captured with).  ST_EINVAL for ns < 0.  Section 5.3
+ * describes the batch of events this kernel runs; the limit itself has no
+ * counterpart in the paper. */
+int st_set_wait_limit(st_ctx* ctx, int64_t ns);
+
 /* Counters of the work done since the last reset (synchronises the device).
  * reset != 0 zeroes them afterwards. */
 int st_read_counters(st_ctx* ctx, st_counters* out, int reset);
@@ -347,18 +363,24 @@ int st_read_counters(st_ctx* ctx, st_counters* out, int reset);
  * caller), cfg replaces the context, and the work runs on the device that is
  * current for the calling thread.  The results equal seeding_run's.
  * Limits: max_hits_per_event <= 6144, and the batch must fit the array:
- * about 8*n_events*max_hits_per_event + 98*seeds->cap bytes plus one
- * candidate store of about 112*cand_cap + 8*max_hits_per_event + 360 KB
+ * (8*max_hits_per_event + 156) bytes per event plus 98*seeds->cap bytes plus
+ * one candidate store of about 112*cand_cap + 8*max_hits_per_event + 360 KB
  * (e.g. 128 events of up to 4096 hits with 40 000 seeds fit); otherwise it
- * returns ST_OVERFLOW and writes nothing.  A NUL-terminated message goes to
- * err (may be NULL) on every failure.
+ * returns ST_OVERFLOW, writes nothing, and the message gives the exact byte
+ * count the batch needs.  A configuration whose shared-memory needs exceed
+ * the device's (the check st_create makes) gives ST_EINVAL.  Launch shapes
+ * follow cfg as in seeding_run, ctas_per_sm included.  A NUL-terminated
+ * message goes to err (may be NULL) on every failure.
  *
  * The first call on a device sets that device up (looks up the array's device
  * address and raises the kernels' shared-memory limits); make that first call
- * before any stream capture.  Every call reuses the same array: work queues
- * and counters are cleared at the start of each call, and calls that overlap
- * on the GPU (different streams or host threads at once) race on it, so
- * serialise them.  Returns ST_OK, ST_EINVAL, ST_OVERFLOW or ST_ECUDA. */
+ * before any stream capture.  Later calls outside a capture check that set-up
+ * again, so a call after cudaDeviceReset sets the device up anew; calls inside
+ * a capture use what the last call outside one found.  Every call reuses the
+ * same array: work queues and counters are cleared at the start of each call,
+ * and calls that overlap on the GPU (different streams or host threads at
+ * once) race on it, so serialise them.  Returns ST_OK, ST_EINVAL, ST_OVERFLOW
+ * or ST_ECUDA. */
 int seeding_run_static(const st_config* cfg, const st_hits* hits, st_seeds* seeds, void* cuda_stream,
                        char* err, int32_t err_len);
 

@@ -25,12 +25,20 @@ CSR gather, matching) with CUDA events, the L2 flushed before every replay:
 The result is a dict of st_config overrides; `st.st_config_default(**tuned)`
 applies it.  `python -m paper_2606_14480_gb300.autotune --help` runs it on a
 synthetic workload and writes the overrides to a JSON file.
+
+The window widths picked on a GB300 are kept in tuned_windows.json beside this
+module (`--write-windows`), so that every process that must agree on them
+(the library's benchmark arm, the CPU reference arm timed in a separate
+process, the parity tests) applies the same values; `tuned_windows()` reads
+them.  The benchmark sweeps the grid again on its own batch and reports
+whether that sweep picks the same point.
 """
 
 from __future__ import annotations
 
 import argparse
 import json
+import os
 import time
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional, Sequence
@@ -57,6 +65,27 @@ WINDOW_GRID: List[Dict[str, float]] = [
     for s in (1.0, 0.9, 0.8)
     for lo, hi in ((0.5, 1.5), (0.6, 1.4), (0.7, 1.3))
 ]
+
+
+TUNED_WINDOWS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_windows.json")
+WINDOW_KEYS = ("dx3_scale", "m_lo", "m_hi", "ext_tol")
+
+
+def tuned_windows(path: str = TUNED_WINDOWS_PATH) -> Dict[str, float]:
+    """The window widths a tuning run picked ({} if there is none): a dict of
+    st_config overrides with keys in WINDOW_KEYS."""
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        d = json.load(f)
+    return {k: float(v) for k, v in d["overrides"].items() if k in WINDOW_KEYS}
+
+
+def tuned_windows_record(path: str = TUNED_WINDOWS_PATH) -> Optional[dict]:
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
 
 
 @dataclass
@@ -284,13 +313,30 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--workload", default="uneven", help="synthetic workload name")
     ap.add_argument("--events", type=int, default=2000, help="calibration events")
+    ap.add_argument("--seed", type=int, default=None, help="generator seed of the calibration batch")
     ap.add_argument("--no-windows", action="store_true", help="tune launch shapes only")
+    ap.add_argument("--write-windows", action="store_true",
+                    help=f"sweep the window grid only and write the pick to {os.path.basename(TUNED_WINDOWS_PATH)}")
     ap.add_argument("--device", type=int, default=0)
     ap.add_argument("--out", default=None, help="write the overrides here (JSON)")
     args = ap.parse_args(argv)
     from synth import calibrate_zmatch, make_workload
-    batch = make_workload(args.workload, n_events=args.events)
+    batch = make_workload(args.workload, n_events=args.events, seed=args.seed)
     zmx = calibrate_zmatch(7826.0)
+    if args.write_windows:
+        wr = tune_windows({"zmx": list(map(float, zmx))}, calibration_from_synth(batch), device=args.device)
+        ref = wr.points[0]
+        best = next(p for p in wr.points if p.overrides == wr.best)
+        rec = {"overrides": wr.best, "ms": best.ms, "eff": best.eff, "ghost": best.ghost,
+               "paper_widths": {"overrides": ref.overrides, "ms": ref.ms, "eff": ref.eff, "ghost": ref.ghost},
+               "budget": {"eff_drop": 0.002, "ghost_rise": 0.002},
+               "calibration": f"{args.workload}, {args.events} events, seed {args.seed}",
+               "grid": [{"overrides": p.overrides, "ms": p.ms, "eff": p.eff, "ghost": p.ghost, "ok": p.ok}
+                        for p in wr.points]}
+        with open(TUNED_WINDOWS_PATH, "w") as f:
+            json.dump(rec, f, indent=1, default=float)
+        print(json.dumps(rec, default=float, indent=1))
+        return
     tuned, report = autotune({"zmx": list(map(float, zmx))}, calibration_from_synth(batch), device=args.device,
                              windows=not args.no_windows)
     tuned.pop("zmx", None)

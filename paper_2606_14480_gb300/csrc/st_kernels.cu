@@ -699,10 +699,18 @@ struct MatchIO {
 };
 template <bool kFinal, class Row>
 __device__ int match_event(const DevParams& P, const MatchIO& M, int VS, unsigned char* msm, int64_t v0, int nv,
-                           int ns, Row row, int* s_cnt, ull& n_grid, ull& n_presel);
+                           int ns, Row row, int* s_cnt, ull& n_grid, ull& n_presel, ull& n_eval);
 
 constexpr int kDeferRounds = 2;       // matching left to idle CTAs once fewer seeding items than this per CTA remain
-constexpr int kReadySpins = 1 << 22;  // polls (100 ns apart) of an announcement before giving up
+// A wait for an announced event ends after SeedArgs::wait_ns of the global
+// timer; the poll count is a second bound in case the timer stalls.
+constexpr int kReadySpinsMax = 1 << 24;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // kSeq: compiled with the HLT2-style pass loop and taken-hit checks; the HLT1
 // instantiation has neither (they fold away).
@@ -772,8 +780,8 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     constexpr bool seq = kSeq;
     const uint32_t* used = kSeq ? g_used : nullptr;
     __shared__ int s_nvalid, s_cnt, s_match;
-    __shared__ ull s_mctr[3];
-    if (kFuse && tid < 3) s_mctr[tid] = 0;
+    __shared__ ull s_mctr[4];  // grid pairs, preselected pairs, Long tracks, evaluated pairs
+    if (kFuse && tid < 4) s_mctr[tid] = 0;
     int spar = 0;  // which half of tmp the next block scan uses
 
     // work counters (pairs, triplets, extended, candidates, kept, UV initial
@@ -816,7 +824,11 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     const volatile int* vr = A.ready;
                     int v = 0;
                     bool gave_up = true;
-                    for (int it = 0; it < kReadySpins; ++it) {
+                    const unsigned long long t_wait = global_ns();
+                    for (int it = 0; it < kReadySpinsMax; ++it) {
+                        // the time limit is checked first: with wait_ns = 0
+                        // every wait gives up (the timeout path, for tests)
+                        if (global_ns() - t_wait >= A.wait_ns) break;
                         if (m < n) v = vr[m];
                         if (v) {
                             gave_up = false;
@@ -848,16 +860,18 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
             const int64_t r1 = c1 ? __ldcg(A.item_start + 2 * em + 1) : 0;
             const int64_t v0 = A.velo_off[em];
             const MatchIO M{A.velo, A.pool_state, A.pool_n, A.pool_velo, A.pool_chi2, nullptr};
-            ull ng = 0, np = 0;
+            ull ng = 0, np = 0, nev = 0;
             const int nl = match_event<false>(P, M, A.velo_smem, smem, v0,
                                                     static_cast<int>(A.velo_off[em + 1] - v0), c0 + c1,
                                                     [&](int s) { return s < c0 ? r0 + s : r1 + (s - c0); },
-                                                    &s_cnt, ng, np);
+                                                    &s_cnt, ng, np, nev);
             ng = warp_sum(ng);
             np = warp_sum(np);
+            nev = warp_sum(nev);
             if ((tid & 31) == 0) {
                 atomicAdd(&s_mctr[0], ng);
                 atomicAdd(&s_mctr[1], np);
+                atomicAdd(&s_mctr[3], nev);
             }
             if (tid == 0) {
                 atomicAdd(&s_mctr[2], ull(nl));
@@ -1370,6 +1384,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     __syncthreads();
     if (tid < 8 && s_ctr[tid]) atomicAdd(A.counters + C_PAIRS + tid, s_ctr[tid]);
     if (kFuse && tid < 3 && s_mctr[tid]) atomicAdd(A.counters + C_MATCH_PAIRS + tid, s_mctr[tid]);
+    if (kFuse && tid == 3 && s_mctr[3]) atomicAdd(A.counters + C_MATCH_EVAL, s_mctr[3]);
 }
 
 // ===========================================================================
@@ -1583,7 +1598,7 @@ __device__ float ghost_nn(const DevParams& P, const float f[8]) {
 // thread's pair counts.
 template <bool kFinal, class Row>
 __device__ int match_event(const DevParams& P, const MatchIO& M, int VS, unsigned char* msm, int64_t v0, int nv,
-                           int ns, Row row, int* s_cnt, ull& n_grid, ull& n_presel) {
+                           int ns, Row row, int* s_cnt, ull& n_grid, ull& n_presel, ull& n_eval) {
     const int T = blockDim.x, tid = threadIdx.x;
     float* vxh = reinterpret_cast<float*>(msm);
     float* vxl = vxh + VS;
@@ -1668,12 +1683,14 @@ __device__ int match_event(const DevParams& P, const MatchIO& M, int VS, unsigne
                 // the exact cut is applied per pair)
                 const float w = P.cut_ty + 1e-6f * (fabsf(tyS) + P.cut_ty);
                 const int k0 = boff[ty_bin(tyS - w)], k1 = boff[ty_bin(tyS + w) + 1];
+                n_eval += k1 - k0;
                 for (int k = k0; k < k1; ++k) {
                     const int v = bidx[k];
                     npre += match_pair(P, vxh[v], vxl[v], vyh[v], vyl[v], vtx[v], vty[v], vit[v], vc + v,
                                        xh, xl, yh, yl, txS, tyS, dzx, best, bv);
                 }
             } else {
+                n_eval += m;
                 for (int v = 0; v < m; ++v)
                     npre += match_pair(P, vxh[v], vxl[v], vyh[v], vyl[v], vtx[v], vty[v], vit[v], vc + v,
                                        xh, xl, yh, yl, txS, tyS, dzx, best, bv);
@@ -1803,7 +1820,7 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
     __shared__ int s_item, s_cnt;
-    ull ctr[3] = {0, 0, 0};
+    ull ctr[4] = {0, 0, 0, 0};  // grid pairs, preselected pairs, Long tracks, evaluated pairs
     const MatchIO M{A.velo, A.seed_state, A.seed_n, A.velo_idx, A.chi2, A.ghost_prob};
 
     for (;;) {
@@ -1817,13 +1834,14 @@ k_match(const __grid_constant__ DevParams P, const __grid_constant__ MatchArgs A
         const int64_t s0 = A.seed_off[e];
         const int ns = A.seed_off[e + 1] - static_cast<int>(s0);
         const int nl = match_event<kFinal>(P, M, A.velo_smem, smem, v0, nv, ns,
-                                           [&](int s) { return s0 + s; }, &s_cnt, ctr[0], ctr[1]);
+                                           [&](int s) { return s0 + s; }, &s_cnt, ctr[0], ctr[1], ctr[3]);
         if (tid == 0) {
             if (A.n_long) A.n_long[e] = nl;
             ctr[2] += nl;
         }
     }
     flush_counters(A.counters + C_MATCH_PAIRS, ctr, 3);
+    flush_counters(A.counters + C_MATCH_EVAL, ctr + 3, 1);
 }
 
 // ===========================================================================
@@ -1849,6 +1867,17 @@ cudaError_t set_smem_limits(size_t optin) {
             return err;
     }
     return cudaSuccess;
+}
+
+// Whether the ceilings set_smem_limits raises are still in place (a
+// cudaDeviceReset drops them with the context): checked on the container
+// kernel, the first one set_smem_limits raises.
+cudaError_t smem_limits_hold(size_t optin, bool& hold) {
+    cudaFuncAttributes fa;
+    const cudaError_t err = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(k_build));
+    hold = err == cudaSuccess &&
+           fa.maxDynamicSharedSizeBytes >= static_cast<int>(optin) - static_cast<int>(fa.sharedSizeBytes);
+    return err;
 }
 
 int build_blocks_per_sm(int threads, size_t smem) {

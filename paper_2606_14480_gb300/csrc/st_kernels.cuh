@@ -11,7 +11,7 @@ namespace st {
 // counters (same order as st_counters)
 enum {
     C_PAIRS = 0, C_TRIPLETS, C_EXT_OK, C_CANDS, C_KEPT, C_UV_INIT, C_UV_CANDS, C_SEEDS,
-    C_MATCH_PAIRS, C_MATCH_PRESEL, C_MATCHED, C_HITS, C_EVENTS, C_N
+    C_MATCH_PAIRS, C_MATCH_PRESEL, C_MATCHED, C_HITS, C_EVENTS, C_MATCH_EVAL, C_N
 };
 
 struct BuildArgs {
@@ -79,6 +79,7 @@ struct SeedArgs {
     int32_t* m_claim = nullptr;    // announcements claimed; zero before
     int32_t* done_ctr = nullptr;   // events with both halves finished; zero before
     int32_t* fault = nullptr;      // set if a wait gave up; zero before
+    unsigned long long wait_ns = 0;  // longest wait for an announced event (globaltimer ns); 0: give up at once
     int32_t* pool_velo = nullptr;  // [pool_cap] matched VELO segment per seed record
     float* pool_chi2 = nullptr;    // [pool_cap]
     int32_t* n_long = nullptr;     // [n_events], may be null
@@ -138,5 +139,6 @@ int build_blocks_per_sm(int threads, size_t smem);
 int seed_blocks_per_sm(int threads, size_t smem);
 int match_blocks_per_sm(int threads, size_t smem);
 cudaError_t set_smem_limits(size_t optin);
+cudaError_t smem_limits_hold(size_t optin, bool& hold);
 
 }  // namespace st

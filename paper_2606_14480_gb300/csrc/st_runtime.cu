@@ -421,6 +421,8 @@ struct Workspace {
 
 struct Pipeline;
 
+constexpr int64_t kDefaultWaitNs = 200000000;  // 200 ms
+
 struct st_ctx {
     st_config cfg;
     DevParams P;
@@ -437,6 +439,7 @@ struct st_ctx {
     std::mutex pipe_mu;
     bool timing = false;
     bool has_nn = false;  // ghost network weights given
+    int64_t wait_ns = kDefaultWaitNs;  // fused seeding kernel: longest wait for an announced event
     cudaEvent_t tev[4][2] = {};
     bool tused[4] = {};
 };
@@ -750,6 +753,7 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
         a.ready = w.ev_done + H.n_events;
         a.ready_ctr = w.queues + 3;
         a.fault = w.queues + 4;
+        a.wait_ns = static_cast<unsigned long long>(ctx->wait_ns);
         a.m_claim = w.queues + 5;
         a.done_ctr = w.queues + 6;
         a.pool_velo = w.pool_velo;
@@ -950,6 +954,13 @@ extern "C" int st_set_timing(st_ctx* ctx, int enable) {
     }
     ctx->timing = enable != 0;
     for (int k = 0; k < 4; ++k) ctx->tused[k] = false;
+    return ST_OK;
+}
+
+extern "C" int st_set_wait_limit(st_ctx* ctx, int64_t ns) {
+    if (!ctx) return ST_EINVAL;
+    if (ns < 0) return set_err(ctx, ST_EINVAL, "st_set_wait_limit: negative limit %lld", (long long)ns);
+    ctx->wait_ns = ns;
     return ST_OK;
 }
 

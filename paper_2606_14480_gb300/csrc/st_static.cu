@@ -12,7 +12,8 @@
 // The array g_scratch below is a `__device__` variable: every GPU that loads
 // the library holds ST_STATIC_SCRATCH_BYTES of it until the process exits.
 // In host code its name is only a host-side stand-in, so the device address is
-// obtained once per device with cudaGetSymbolAddress (with that device current)
+// obtained with cudaGetSymbolAddress (with that device current) on the first
+// call per device, checked again on later calls made outside stream capture,
 // and passed to the kernels as a pointer.
 #include <algorithm>
 #include <cstdarg>
@@ -38,6 +39,7 @@ struct DeviceSetup {
     bool done = false;
     unsigned char* base = nullptr;  // device address of g_scratch on this device
     int n_sms = 0;
+    int optin = 0;                  // opt-in shared memory per CTA
 };
 
 std::mutex g_mu;
@@ -55,23 +57,34 @@ int fail(char* err, int err_len, int code, const char* fmt, ...) {
 
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// once per device, with that device current
-int setup_device(int dev, DeviceSetup*& out, char* err, int err_len) {
+// With `dev` current.  The first call on a device looks up the array's
+// device address and raises the kernels' shared-memory ceilings.  Later calls
+// outside stream capture check both again, since a cudaDeviceReset in between
+// ends the context that held them: the address is looked up anew and the
+// ceilings raised again if they are gone.  Inside a capture the cached values
+// are used (the first call must come before any capture).
+int setup_device(int dev, bool capturing, DeviceSetup*& out, char* err, int err_len) {
     std::lock_guard<std::mutex> g(g_mu);
     DeviceSetup& S = g_setup[dev];
-    if (!S.done) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess)
-            return fail(err, err_len, ST_ECUDA, "cudaGetSymbolAddress(g_scratch): %s", cudaGetErrorString(e));
-        int optin = 0;
-        e = cudaDeviceGetAttribute(&S.n_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e == cudaSuccess) e = set_smem_limits(optin);
-        if (e != cudaSuccess) return fail(err, err_len, ST_ECUDA, "device set-up: %s", cudaGetErrorString(e));
-        S.base = static_cast<unsigned char*>(p);
-        S.done = true;
+    if (S.done && capturing) {
+        out = &S;
+        return ST_OK;
     }
+    if (!S.done) {
+        cudaError_t e = cudaDeviceGetAttribute(&S.n_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return fail(err, err_len, ST_ECUDA, "device set-up: %s", cudaGetErrorString(e));
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess)
+        return fail(err, err_len, ST_ECUDA, "cudaGetSymbolAddress(g_scratch): %s", cudaGetErrorString(e));
+    bool hold = false;
+    e = smem_limits_hold(size_t(S.optin), hold);
+    if (e == cudaSuccess && !hold) e = set_smem_limits(size_t(S.optin));
+    if (e != cudaSuccess) return fail(err, err_len, ST_ECUDA, "device set-up: %s", cudaGetErrorString(e));
+    S.base = static_cast<unsigned char*>(p);
+    S.done = true;
     out = &S;
     return ST_OK;
 }
@@ -97,10 +110,13 @@ extern "C" int seeding_run_static(const st_config* cfg, const st_hits* H, st_see
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(err, err_len, ST_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(err, err_len, ST_EINVAL, "device index %d out of range", dev);
-    DeviceSetup* D = nullptr;
-    int rc = setup_device(dev, D, err, err_len);
-    if (rc != ST_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap_st);
+    if (e != cudaSuccess) return fail(err, err_len, ST_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+    DeviceSetup* D = nullptr;
+    int rc = setup_device(dev, cap_st != cudaStreamCaptureStatusNone, D, err, err_len);
+    if (rc != ST_OK) return rc;
 
     // carve the static array for this batch
     const int64_t ne = H->n_events, mh = H->max_hits_per_event, items = 2 * ne;
@@ -150,11 +166,20 @@ extern "C" int seeding_run_static(const st_config* cfg, const st_hits* H, st_see
     int bins = 8;
     while (bins < 512 && bins * 96 < mh) bins <<= 1;
     const size_t bsmem = build_smem_bytes(bins, static_cast<int>(mh));
-    const int bbps = std::max(1, build_blocks_per_sm(cfg->threads_build, bsmem));
-    const int g_build = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ne, int64_t(D->n_sms) * bbps)));
     const int tbl_smem = cfg->smem_hits / 2, key_smem = std::max(64, cfg->smem_hits / 6);  // as st_create
     const size_t ssmem = seed_smem_bytes(cfg->threads_seed, cfg->smem_hits, tbl_smem, key_smem);
-    const int sbps = std::max(1, seed_blocks_per_sm(cfg->threads_seed, ssmem));
+    // the shared-memory check of st_create (2 KB left for static shared memory)
+    if (ssmem + 2048 > size_t(D->optin) || bsmem + 2048 > size_t(D->optin))
+        return fail(err, err_len, ST_EINVAL,
+                    "config needs %zu (seeding) / %zu (containers) bytes of shared memory per CTA; the device "
+                    "allows %d", ssmem, bsmem, D->optin);
+    int bbps = std::max(1, build_blocks_per_sm(cfg->threads_build, bsmem));
+    int sbps = std::max(1, seed_blocks_per_sm(cfg->threads_seed, ssmem));
+    if (cfg->ctas_per_sm > 0) {  // as seeding_run
+        bbps = std::min(bbps, cfg->ctas_per_sm);
+        sbps = std::min(sbps, cfg->ctas_per_sm);
+    }
+    const int g_build = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ne, int64_t(D->n_sms) * bbps)));
     const int g_seed = static_cast<int>(
         std::max<int64_t>(1, std::min<int64_t>({items, int64_t(D->n_sms) * sbps, slots_fit})));
 

@@ -75,7 +75,7 @@ class StUtOut(C.Structure):
 
 
 COUNTER_NAMES = ("pairs", "triplets", "ext_ok", "cands", "kept", "uv_init", "uv_cands", "seeds",
-                 "match_pairs", "match_presel", "matched", "hits", "events")
+                 "match_pairs", "match_presel", "matched", "hits", "events", "match_eval")
 
 
 class StCounters(C.Structure):
@@ -113,6 +113,7 @@ SIGNATURES = {
     "st_graph_destroy": ([_P], None),
     "st_read_counters": ([_P, C.POINTER(StCounters), C.c_int], C.c_int),
     "st_set_timing": ([_P, C.c_int], C.c_int),
+    "st_set_wait_limit": ([_P, C.c_int64], C.c_int),
     "st_set_ghost_nn": ([_P, _P, C.c_int32], C.c_int),
     "ut_run": ([_P, C.POINTER(StVelo), C.POINTER(StSeeds), C.POINTER(StUtHits), C.POINTER(StLong),
                 C.POINTER(StUtOut), _P], C.c_int),
@@ -253,6 +254,9 @@ class Context:
 
     def st_set_timing(self, enable=True):
         return self._check(self.lib.st_set_timing(self.h, int(enable)), "st_set_timing")
+
+    def st_set_wait_limit(self, ns):
+        return self._check(self.lib.st_set_wait_limit(self.h, int(ns)), "st_set_wait_limit")
 
     def st_kernel_ms(self):
         ms = (C.c_float * 4)()

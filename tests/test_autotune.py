@@ -81,6 +81,24 @@ def test_search_spaces_hold_the_defaults():
     assert len({tuple(sorted(p.items())) for p in autotune.WINDOW_GRID}) == len(autotune.WINDOW_GRID)
 
 
+def test_tuned_windows_record():
+    """The committed window pick is a grid point within the tuner's budget,
+    and the benchmark's arms read it the same way."""
+    rec = autotune.tuned_windows_record()
+    if rec is None:
+        pytest.skip("no tuned_windows.json")
+    w = autotune.tuned_windows()
+    assert set(w) <= set(autotune.WINDOW_KEYS)
+    assert any(all(abs(p[k] - w[k]) < 1e-12 for k in w) for p in autotune.WINDOW_GRID)
+    ref = rec["paper_widths"]
+    assert ref["overrides"] == autotune.WINDOW_GRID[0]
+    assert rec["eff"] >= ref["eff"] - rec["budget"]["eff_drop"]
+    assert rec["ghost"] <= ref["ghost"] + rec["budget"]["ghost_rise"]
+    picked = [p for p in rec["grid"] if p["overrides"] == rec["overrides"]]
+    assert len(picked) == 1 and picked[0]["ok"]
+    assert all(p["ms"] >= rec["ms"] for p in rec["grid"] if p["ok"])
+
+
 # ------------------------------------------------------------------- GPU
 
 def _gpu():
@@ -139,3 +157,30 @@ def test_window_tuning_picks_within_budget():
     assert 0.9 < ref.eff <= 1.0 and 0.0 <= ref.ghost < 0.1
     pick = next(p for p in r.points if p.overrides == r.best)
     assert pick.eff >= ref.eff - 0.002 and pick.ghost <= ref.ghost + 0.002
+
+
+@pytest.mark.gpu
+def test_applied_windows_full_size_parity():
+    """The benchmark's configuration: the full 1000-event Run-3-like batch at
+    the applied (tuned) window widths, the oracle at the same values on a
+    sample of 48 events, seeding and matching."""
+    _gpu()
+    import parity
+    from paper_2606_14480_gb300 import st
+    from synth import calibrate_zmatch
+    w = autotune.tuned_windows()
+    b = workload("run3")
+    zmx = calibrate_zmatch(7826.0)
+    ocfg, gcfg = parity.config_pair(zmx, **w)
+    ctx = st.Context(gcfg)
+    out = st.run_batch(ctx, st.DeviceBatch.from_synth(b))
+    gpu = out.to_numpy()
+    ctx.close()
+    assert (gpu["status"] == 0).all()
+    rng = np.random.default_rng(17)
+    ev = np.sort(rng.choice(b.n_events, 48, replace=False))
+    rep = parity.compare_seeding(gpu, ocfg, b, ev)
+    print(w, rep.summary())
+    parity.assert_seeding(rep)
+    n, untraced, traced, _ = parity.compare_matching(gpu, ocfg, b, ev)
+    assert not untraced, untraced[:5]

@@ -53,6 +53,47 @@ def test_static_scratch_seeding_equals_seeding_run():
     ctx.close()
 
 
+def test_static_scratch_call_allocates_nothing():
+    """After a first call (which may load the kernels' code on the device), a
+    further call leaves the device's free memory unchanged: nothing is
+    allocated, by the library or by anything it calls.  Every buffer the
+    calls use is made before the first reading."""
+    cfg = st.st_config_default()
+    b = make_workload("run3", n_events=32, seed=2004)
+    db = st.DeviceBatch.from_synth(b)
+    outs = [st.DeviceOutputs(b.n_events, max(1024, b.n_hits // 4)) for _ in range(2)]
+    rc, msg = st.seeding_run_static(cfg, db.hits, outs[0].seeds)
+    assert rc == st.ST_OK, msg
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rc, msg = st.seeding_run_static(cfg, db.hits, outs[1].seeds)
+        assert rc == st.ST_OK, msg
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    _outputs_equal(outs[0].to_numpy(), outs[1].to_numpy())
+
+
+def test_static_scratch_checks_shared_memory_and_launch_shape():
+    """A configuration that st_create refuses for its shared memory is refused
+    here too, before anything runs; ctas_per_sm changes the launch shape, not
+    the result."""
+    b = make_workload("tiny", n_events=10, seed=2005)
+    db = st.DeviceBatch.from_synth(b)
+    out = st.DeviceOutputs(b.n_events, 2048)
+    rc, msg = st.seeding_run_static(st.st_config_default(smem_hits=32768), db.hits, out.seeds)
+    assert rc == st.ST_EINVAL and "shared memory" in msg, (rc, msg)
+    res = []
+    for cps in (0, 1):
+        o = st.DeviceOutputs(b.n_events, 2048)
+        rc, msg = st.seeding_run_static(st.st_config_default(ctas_per_sm=cps), db.hits, o.seeds)
+        assert rc == st.ST_OK, msg
+        torch.cuda.synchronize()
+        res.append(o.to_numpy())
+    _outputs_equal(res[0], res[1])
+
+
 def test_static_scratch_rejects_oversized_batch():
     cfg = st.st_config_default()
     b = make_workload("tiny", n_events=10, seed=2003)
