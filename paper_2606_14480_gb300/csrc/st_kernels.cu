@@ -82,66 +82,82 @@ __device__ __forceinline__ void set_item_class(const BuildArgs& A, int64_t item,
     atomicAdd(A.class_count + c, 1);
 }
 
+// shared memory of k_build: bucket counts / fill cursors and bucket starts,
+// the block scan's scratch, then 8 bytes per hit (x, bucket -> final place,
+// permutation)
 size_t build_smem_bytes(int bins, int smem_hits) {
     const int NB = kZones * bins;
-    return align16(sizeof(int) * (2 * NB + 1 + 36)) + align16(size_t(10) * smem_hits);
+    return align16(sizeof(int) * (2 * NB + 1 + 36)) + align16(size_t(8) * smem_hits);
 }
 
-// at most 32 registers: four 512-thread CTAs per SM (a 1000-event batch in two rounds)
+// Per event (one CTA): validate and bucket the hits by (container slot, x),
+// place them bucket by bucket, rank each hit inside its bucket by (x, index)
+// and write the sorted event out in order.  Per-hit arrays: x (hx), bucket
+// and then final place (bk), and a permutation (pm): first the hits grouped
+// by bucket, then the sorted order.  Between two events of a CTA the bucket
+// counts are cleared during the ranking and the next event's ticket and
+// offsets are fetched during the placement, so the next event starts with
+// its loads.  At most 32 registers: up to eight 256-thread CTAs per SM.
 __global__ void __launch_bounds__(kMaxThreads, 4)
 k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = A.bins, NB = kZones * B, T = blockDim.x, tid = threadIdx.x;
-    int* cnt = reinterpret_cast<int*>(smem);
+    int* cnt = reinterpret_cast<int*>(smem);  // counts, then fill cursors, then cleared
     int* off = cnt + NB;
     int* tmp = off + NB + 1;
     unsigned char* harea = smem + align16(sizeof(int) * (2 * NB + 1 + 36));
-    // s_item: the CTA's next event.  Thread 0 takes its queue ticket while the
-    // current event is still being sorted (during the placement; it is
-    // published at the end), so the atomic's round trip does not stand
-    // between two events.
+    // the CTA's next event and its hit range, published by thread 0
     __shared__ int s_item, s_bad;
+    __shared__ long long s_h0, s_h1;
     ull ctr[2] = {0, 0};
-    int q_next = 0;
-    if (tid == 0) s_item = atomicAdd(A.queue, 1);
+    for (int k = tid; k < NB; k += T) cnt[k] = 0;
+    if (tid == 0) {
+        s_bad = 0;
+        s_item = atomicAdd(A.queue, 1);
+        if (s_item < A.n_events) {
+            s_h0 = A.ev_off[s_item];
+            s_h1 = A.ev_off[s_item + 1];
+        }
+    }
+    // thread 0: the next ticket and the offsets of its event
+    auto next_item = [&]() {
+        const int q = atomicAdd(A.queue, 1);
+        if (q < A.n_events) {
+            s_h0 = A.ev_off[q];
+            s_h1 = A.ev_off[q + 1];
+        }
+        s_item = q;
+    };
 
     for (;;) {
         __syncthreads();
         const int64_t e = s_item;
         if (e >= A.n_events) break;
-        const int64_t h0 = A.ev_off[e];
-        const int64_t n64 = A.ev_off[e + 1] - h0;
+        const int64_t h0 = s_h0;
+        const int64_t n64 = s_h1 - h0;
         int32_t* zo = A.zoff + e * kZoffStride;
-        if (n64 < 0 || n64 > A.max_hits) {
+        const int64_t cb = cont_base(A.ev_off, e);
+        if (n64 < 0 || n64 > A.max_hits || cb + n64 > A.cont_cap) {
+            // too large for max_hits, or an earlier oversized event pushed this
+            // one past the container
             for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
-            if (tid == 0) A.status[e] = -3;  // ST_OVERFLOW
             if (tid < 2) set_item_class(A, 2 * e + tid, 0);
             __syncthreads();  // every thread has read s_item
-            if (tid == 0) s_item = atomicAdd(A.queue, 1);
+            if (tid == 0) {
+                A.status[e] = -3;  // ST_OVERFLOW
+                next_item();
+            }
             continue;
         }
         const int n = static_cast<int>(n64);
-        const int64_t cb = cont_base(A.ev_off, e);
-        if (cb + n > A.cont_cap) {  // an earlier oversized event pushed this one past the container
-            for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
-            if (tid == 0) A.status[e] = -3;  // ST_OVERFLOW
-            if (tid < 2) set_item_class(A, 2 * e + tid, 0);
-            __syncthreads();
-            if (tid == 0) s_item = atomicAdd(A.queue, 1);
-            continue;
-        }
         const bool in_smem = n <= A.smem_hits;
         unsigned char* base = in_smem ? harea : A.big + int64_t(blockIdx.x) * A.big_stride;
         const int cap = in_smem ? A.smem_hits : A.max_hits;
         float* hx = reinterpret_cast<float*>(base);
         uint16_t* bk = reinterpret_cast<uint16_t*>(hx + cap);
-        uint16_t* rk = bk + cap;
-        uint16_t* pm = rk + cap;
-        for (int k = tid; k < NB; k += T) cnt[k] = 0;
-        if (tid == 0) s_bad = 0;
-        __syncthreads();
+        uint16_t* pm = bk + cap;
         const float binscale = B / (2.f * kBinRange);
-        // four hits per thread per round, their loads issued together
+        // count: four hits per thread per round, their loads issued together
         for (int i0 = tid; i0 < n; i0 += 4 * T) {
             float xs[4];
             int zs[4];
@@ -172,18 +188,23 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
                 const int b = P.slot_of_zone[zn] * B + bin;
                 hx[i] = x;
                 bk[i] = static_cast<uint16_t>(b);
-                rk[i] = static_cast<uint16_t>(atomicAdd(&cnt[b], 1));
+                atomicAdd(&cnt[b], 1);
             }
         }
         __syncthreads();
         if (s_bad) {
             for (int k = tid; k < kZoffStride; k += T) zo[k] = 0;
-            if (tid == 0) A.status[e] = -1;  // ST_EINVAL
+            for (int k = tid; k < NB; k += T) cnt[k] = 0;
             if (tid < 2) set_item_class(A, 2 * e + tid, 0);
-            if (tid == 0) s_item = atomicAdd(A.queue, 1);  // s_item was read before the barrier above
+            __syncthreads();  // s_bad read by every thread
+            if (tid == 0) {
+                A.status[e] = -1;  // ST_EINVAL
+                s_bad = 0;
+                next_item();
+            }
             continue;
         }
-        {   // exclusive scan of the bucket counts
+        {   // exclusive scan of the bucket counts; the counts become fill cursors
             const int per = (NB + T - 1) / T;
             const int k0 = min(tid * per, NB), k1 = min(k0 + per, NB);
             int sum = 0;
@@ -191,19 +212,23 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
             int tot;
             int ex = block_exscan(sum, tmp, tot);
             for (int k = k0; k < k1; ++k) {
+                const int c = cnt[k];
                 off[k] = ex;
-                ex += cnt[k];
+                cnt[k] = ex;
+                ex += c;
             }
             if (tid == 0) off[NB] = tot;
         }
         __syncthreads();
-        if (tid == 0) q_next = atomicAdd(A.queue, 1);  // published after the output
-        for (int i = tid; i < n; i += T) pm[off[bk[i]] + rk[i]] = static_cast<uint16_t>(i);
+        if (tid == 0) next_item();  // read by the other threads after the next loop-top barrier
+        for (int i = tid; i < n; i += T) pm[atomicAdd(&cnt[bk[i]], 1)] = static_cast<uint16_t>(i);
         __syncthreads();
-        // rank of each hit in its bucket -> its place in the sorted event, kept
-        // in rk (which no other thread reads from here on)
+        // rank of each hit in its bucket -> its place in the sorted event (in
+        // bk[i], which only this thread reads); the cursors are cleared for
+        // the next event
+        for (int k = tid; k < NB; k += T) cnt[k] = 0;
         for (int i = tid; i < n; i += T) {
-            const int b = bk[i], s = off[b], c = cnt[b];
+            const int b = bk[i], s = off[b], c = off[b + 1] - s;
             const float x = hx[i];
             int r = 0;
             for (int k = s; k < s + c; ++k) {
@@ -211,13 +236,12 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
                 const float xj = hx[j];
                 r += (xj < x) || (xj == x && j < i);
             }
-            rk[i] = static_cast<uint16_t>(s + r);
+            bk[i] = static_cast<uint16_t>(s + r);
         }
         __syncthreads();
-        for (int i = tid; i < n; i += T) pm[rk[i]] = static_cast<uint16_t>(i);
+        for (int i = tid; i < n; i += T) pm[bk[i]] = static_cast<uint16_t>(i);
         __syncthreads();
-        // the sorted event goes out in order (coalesced stores; scattered
-        // stores from the ranking took a third of the kernel's time)
+        // the sorted event goes out in order (coalesced stores)
         for (int d = tid; d < n; d += T) {
             const int i = pm[d];
             A.cx[cb + d] = hx[i];
@@ -234,7 +258,6 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
             A.status[e] = 0;
             ctr[0] += n;
             ctr[1] += 1;
-            s_item = q_next;
         }
     }
     flush_counters(A.counters + C_HITS, ctr, 2);

@@ -73,11 +73,14 @@ def test_match_stress_full_size_sweep(which, s, zmx, stress):
     b, db, out, seeds = stress
     ocfg, gcfg = parity.config_pair(zmx, **{which: s})
     ctx = st.Context(gcfg)
+    ctx.seeding_run(db.hits, out.seeds)  # matching needs this context's seeding (the seeds do not change)
     ctx.matching_run(db.velo_s, out.seeds, out.long)
     torch.cuda.synchronize()
     got = out.to_numpy()
     cnt = ctx.st_read_counters()
     ctx.close()
+    for k in ("ev_off", "hits", "params", "state", "n_hits"):
+        assert np.array_equal(got[k], seeds[k]), k
     assert cnt["match_pairs"] == sum(int(b.velo_off[e + 1] - b.velo_off[e]) * int(seeds["ev_off"][e + 1] -
                                      seeds["ev_off"][e]) for e in range(b.n_events))
     assert 0 < cnt["match_eval"] <= cnt["match_pairs"]
