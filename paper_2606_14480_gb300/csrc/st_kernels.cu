@@ -109,6 +109,15 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
     // the CTA's next event and its hit range, published by thread 0
     __shared__ int s_item, s_bad;
     __shared__ long long s_h0, s_h1;
+    // per-zone / per-layer constants indexed by each hit's zone: in shared
+    // memory (reads of kernel parameters at lane-dependent indices serialise)
+    __shared__ int s_slot[kZones];
+    __shared__ float s_zl[kLayers], s_tl[kLayers];
+    if (tid < kZones) s_slot[tid] = P.slot_of_zone[tid];
+    if (tid < kLayers) {
+        s_zl[tid] = P.zl[tid];
+        s_tl[tid] = P.tl[tid];
+    }
     ull ctr[2] = {0, 0};
     for (int k = tid; k < NB; k += T) cnt[k] = 0;
     if (tid == 0) {
@@ -176,8 +185,8 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
                 bool bad = !(zn >= 0 && zn < kZones) || !isfinite(x);
                 if (!bad) {
                     const int L = zn >> 1;
-                    if (A.z && !(fabsf(A.z[h0 + i] - P.zl[L]) <= 1e-3f)) bad = true;
-                    if (A.dxdy && !(fabsf(A.dxdy[h0 + i] - P.tl[L]) <= 1e-6f)) bad = true;
+                    if (A.z && !(fabsf(A.z[h0 + i] - s_zl[L]) <= 1e-3f)) bad = true;
+                    if (A.dxdy && !(fabsf(A.dxdy[h0 + i] - s_tl[L]) <= 1e-6f)) bad = true;
                 }
                 if (bad) {
                     s_bad = 1;
@@ -185,7 +194,7 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
                 }
                 int bin = __float2int_rd((x + kBinRange) * binscale);
                 bin = min(max(bin, 0), B - 1);
-                const int b = P.slot_of_zone[zn] * B + bin;
+                const int b = s_slot[zn] * B + bin;
                 hx[i] = x;
                 bk[i] = static_cast<uint16_t>(b);
                 atomicAdd(&cnt[b], 1);

@@ -92,7 +92,7 @@ def test_match_stress_full_size_sweep(which, s, zmx, stress):
     n, untraced, traced, chi_rel = parity.compare_matching(got, ocfg, b, ev)
     print(which, s, "seeds", n, "traced", traced, "evaluated/grid", cnt["match_eval"] / cnt["match_pairs"])
     assert n > 0 and not untraced, (untraced[:5], traced)
-    assert traced <= parity.hop_max(n)
+    assert traced <= (1.0 - parity.AGREE_MIN) * n
     assert chi_rel <= 1e-5
 
 

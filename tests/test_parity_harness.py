@@ -77,7 +77,7 @@ def test_dropped_seed_classified(sample):
     assert len(rep.untraced) == 1 and rep.traced == 0
     assert rep.untraced[0][2] == "oracle"
     rep = parity.compare_seeding_event(e, gd, r, tau=float(on["margin"].min()))
-    assert not rep.untraced and rep.traced == 1 and rep.traced_hop == 0
+    assert not rep.untraced and rep.traced == 1 and rep.traced_kinds
 
 
 def test_parameter_beyond_tolerance(sample):
