@@ -83,18 +83,18 @@ __device__ __forceinline__ void set_item_class(const BuildArgs& A, int64_t item,
 }
 
 // shared memory of k_build: bucket counts / fill cursors and bucket starts,
-// the block scan's scratch, then 8 bytes per hit (x, bucket -> final place,
-// permutation)
+// the block scan's scratch, then 10 bytes per hit (x, bucket, the hits
+// grouped by bucket, the sorted order)
 size_t build_smem_bytes(int bins, int smem_hits) {
     const int NB = kZones * bins;
-    return align16(sizeof(int) * (2 * NB + 1 + 36)) + align16(size_t(8) * smem_hits);
+    return align16(sizeof(int) * (2 * NB + 1 + 36)) + align16(size_t(10) * smem_hits);
 }
 
 // Per event (one CTA): validate and bucket the hits by (container slot, x),
 // place them bucket by bucket, rank each hit inside its bucket by (x, index)
 // and write the sorted event out in order.  Per-hit arrays: x (hx), bucket
-// and then final place (bk), and a permutation (pm): first the hits grouped
-// by bucket, then the sorted order.  Between two events of a CTA the bucket
+// (bk), the hits grouped by bucket (pm) and the sorted order (so), which the
+// ranking fills directly.  Between two events of a CTA the bucket
 // counts are cleared during the ranking and the next event's ticket and
 // offsets are fetched during the placement, so the next event starts with
 // its loads.  At most 32 registers: up to eight 256-thread CTAs per SM.
@@ -119,6 +119,7 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
         s_tl[tid] = P.tl[tid];
     }
     ull ctr[2] = {0, 0};
+    int spar = 0;  // which half of tmp the next block scan uses
     for (int k = tid; k < NB; k += T) cnt[k] = 0;
     if (tid == 0) {
         s_bad = 0;
@@ -165,6 +166,7 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
         float* hx = reinterpret_cast<float*>(base);
         uint16_t* bk = reinterpret_cast<uint16_t*>(hx + cap);
         uint16_t* pm = bk + cap;
+        uint16_t* so = pm + cap;
         const float binscale = B / (2.f * kBinRange);
         // count: four hits per thread per round, their loads issued together
         for (int i0 = tid; i0 < n; i0 += 4 * T) {
@@ -219,7 +221,7 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
             int sum = 0;
             for (int k = k0; k < k1; ++k) sum += cnt[k];
             int tot;
-            int ex = block_exscan(sum, tmp, tot);
+            int ex = block_exscan1(sum, tmp, spar, tot);
             for (int k = k0; k < k1; ++k) {
                 const int c = cnt[k];
                 off[k] = ex;
@@ -232,9 +234,8 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
         if (tid == 0) next_item();  // read by the other threads after the next loop-top barrier
         for (int i = tid; i < n; i += T) pm[atomicAdd(&cnt[bk[i]], 1)] = static_cast<uint16_t>(i);
         __syncthreads();
-        // rank of each hit in its bucket -> its place in the sorted event (in
-        // bk[i], which only this thread reads); the cursors are cleared for
-        // the next event
+        // rank of each hit in its bucket -> its place in the sorted event;
+        // the cursors are cleared for the next event
         for (int k = tid; k < NB; k += T) cnt[k] = 0;
         for (int i = tid; i < n; i += T) {
             const int b = bk[i], s = off[b], c = off[b + 1] - s;
@@ -245,14 +246,12 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
                 const float xj = hx[j];
                 r += (xj < x) || (xj == x && j < i);
             }
-            bk[i] = static_cast<uint16_t>(s + r);
+            so[s + r] = static_cast<uint16_t>(i);
         }
-        __syncthreads();
-        for (int i = tid; i < n; i += T) pm[bk[i]] = static_cast<uint16_t>(i);
         __syncthreads();
         // the sorted event goes out in order (coalesced stores)
         for (int d = tid; d < n; d += T) {
-            const int i = pm[d];
+            const int i = so[d];
             A.cx[cb + d] = hx[i];
             A.corig[cb + d] = i;
         }

@@ -511,7 +511,7 @@ static size_t carve(st_ctx* ctx, Workspace& w, int64_t ne, int64_t nh, int32_t m
     char* cx = take(sizeof(float) * size_t(nh + 3 * ne + 8));
     char* co = take(sizeof(int32_t) * size_t(nh + 3 * ne + 8));
     char* zo = take(sizeof(int32_t) * size_t(ne) * kZoffStride + 4);
-    const int64_t big_stride = mh > kBuildSmemHits ? int64_t(al256(size_t(8) * mh)) : 0;
+    const int64_t big_stride = mh > kBuildSmemHits ? int64_t(al256(size_t(10) * mh)) : 0;
     char* big = take(size_t(big_stride) * build_ctas + 16);
     const int64_t slot_stride = int64_t(al256(seed_slot_bytes(ctx->cfg.cand_cap, mh)));
     char* slot = take(size_t(slot_stride) * seed_ctas);
