@@ -359,6 +359,30 @@ __device__ __forceinline__ bool is_used(const uint32_t* used, int p) {
     return used && ((used[p >> 5] >> (p & 31)) & 1u);
 }
 
+// The closest hit to xp within tol in a sorted zone (xs, its bucket table
+// lz, n hits starting at half-local position st), ties to the smaller x (the
+// first met), skipping hits taken by earlier iterations; its half-local
+// position, or -1.  One scan from the table entry of xp - tol: hits below
+// xp - tol are passed over (the window start a zlo search would give), the
+// scan ends at the first hit above xp + tol.
+__device__ __forceinline__ int closest_hit(const float* xs, const uint16_t* lz, int n, int st, float xp, float tol,
+                                           const uint32_t* used) {
+    const float lo = xp - tol, hi = xp + tol;
+    int best = -1;
+    float bd = 0.f;
+    for (int k = lz[lut_bin(lo)]; k < n; ++k) {
+        const float xh = xs[k];
+        if (xh > hi) break;
+        if (xh < lo || is_used(used, st + k)) continue;
+        const float d = fabsf(xh - xp);
+        if (d <= tol && (best < 0 || d < bd)) {
+            best = st + k;
+            bd = d;
+        }
+    }
+    return best;
+}
+
 struct Trip {
     int pos[6];
     float th[3], dth[3];
@@ -394,21 +418,8 @@ __device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, co
             p = p3;
         } else {
             const float xp = fmaf(c3, P.xf_hi[s], fmaf(b3, P.xzb[s], a3));
-            const int st = szl[s], n = szl[s + 1] - st;
-            const float* xs = X + st;
-            int k = zlo(xs, lut + s * kLutBins, n, xp - P.ext_tol);
-            p = -1;
-            float bd = 0.f;
-            for (; k < n; ++k) {
-                const float xh = xs[k];
-                if (xh > xp + P.ext_tol) break;
-                if (is_used(used, st + k)) continue;
-                const float d = fabsf(xh - xp);
-                if (d <= P.ext_tol && (p < 0 || d < bd)) {
-                    p = st + k;
-                    bd = d;
-                }
-            }
+            const int st = szl[s];
+            p = closest_hit(X + st, lut + s * kLutBins, szl[s + 1] - st, st, xp, P.ext_tol, used);
             nx += p >= 0;
         }
         o.pos[s] = p;
@@ -488,21 +499,8 @@ __device__ void uv_chain(const DevParams& P, const float* X, const int* szl, con
         }
         const float Xl = Xs[u];
         const float xp = Xl - P.ut[u] * ty * P.uz[u];
-        const int st = szl[6 + u], nn = szl[7 + u] - st;
-        const float* xs = X + st;
-        int k = zlo(xs, lut + (6 + u) * kLutBins, nn, xp - P.uv_tol);
-        int best = -1;
-        float bd = 0.f;
-        for (; k < nn; ++k) {
-            const float xh = xs[k];
-            if (xh > xp + P.uv_tol) break;
-            if (is_used(used, st + k)) continue;
-            const float d = fabsf(xh - xp);
-            if (d <= P.uv_tol && (best < 0 || d < bd)) {
-                best = st + k;
-                bd = d;
-            }
-        }
+        const int st = szl[6 + u];
+        const int best = closest_hit(X + st, lut + (6 + u) * kLutBins, szl[7 + u] - st, st, xp, P.uv_tol, used);
         if (best >= 0) {
             const float yl = (Xl - X[best]) * P.uinv_t[u];
             ty = 0.5f * fmaf(yl, P.uinv_z[u], ty);
@@ -571,21 +569,8 @@ __device__ void uv_hough(const DevParams& P, const float* X, const int* szl, con
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
         const float xp = Xs[u] - P.ut[u] * ty * P.uz[u];
-        const int st = szl[6 + u], nn = szl[7 + u] - st;
-        const float* xs = X + st;
-        int k = zlo(xs, lut + (6 + u) * kLutBins, nn, xp - P.uv_tol);
-        int best = -1;
-        float bd = 0.f;
-        for (; k < nn; ++k) {
-            const float xh = xs[k];
-            if (xh > xp + P.uv_tol) break;
-            if (is_used(used, st + k)) continue;
-            const float d = fabsf(xh - xp);
-            if (d <= P.uv_tol && (best < 0 || d < bd)) {
-                best = st + k;
-                bd = d;
-            }
-        }
+        const int st = szl[6 + u];
+        const int best = closest_hit(X + st, lut + (6 + u) * kLutBins, szl[7 + u] - st, st, xp, P.uv_tol, used);
         o.pos[u] = best;
         n += best >= 0;
         if (n + (5 - u) < P.n_uv_min) {
