@@ -671,13 +671,19 @@ __device__ __forceinline__ int pair_window(const DevParams& P, const IterP& I, c
     const float ulo = fmaf(I.mlo_k, ip, -I.c0), uhi = fmaf(I.mhi_k, ip, I.c0);
     const float bs = fmaf(I.dz21, t13, x1);
     const float xa = fmaf(I.k3, -sg * ulo, bs), xb = fmaf(I.k3, -sg * uhi, bs);
-    lo2 = zlo(x2, l2, n2, fminf(xa, xb));
-    // the window is narrow (most hold no hit): its end by a forward scan
-    // from its start, not a second table search
-    const float hi = fmaxf(xa, xb);
-    int e = lo2;
-    while (e < n2 && !(hi < x2[e])) ++e;
-    return e - lo2;
+    // the window is narrow (most hold no hit): one forward scan from the
+    // bucket-table entry of its start passes the hits below it and counts
+    // those in it (lo2 matters only when some are)
+    const float lo = fminf(xa, xb), hi = fmaxf(xa, xb);
+    int c = 0;
+    for (int k = l2[lut_bin(lo)]; k < n2; ++k) {
+        const float x = x2[k];
+        if (hi < x) break;
+        if (x < lo) continue;
+        if (c == 0) lo2 = k;
+        ++c;
+    }
+    return c;
 }
 
 constexpr int kTripPerCand = 2;  // triplet buffer entries per candidate slot
@@ -1178,9 +1184,13 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 const float t = P.ut[ui];
                 const float xa = fmaf(-P.uv_yhi[h], t, Xi), xb = fmaf(-P.uv_ylo[h], t, Xi);
                 const int st = szl[6 + ui], n = szl[7 + ui] - st;
-                const uint16_t* lz = lut + (6 + ui) * kLutBins;
-                lo = zlo(X + st, lz, n, fminf(xa, xb));
-                cntc = zhi(X + st, lz, n, fmaxf(xa, xb)) - lo;
+                // the window holds a few hits: its end by a forward scan
+                const float wlo = fminf(xa, xb), whi = fmaxf(xa, xb);
+                const float* xs = X + st;
+                lo = zlo(xs, lut + (6 + ui) * kLutBins, n, wlo);
+                int e = lo;
+                while (e < n && !(whi < xs[e])) ++e;
+                cntc = e - lo;
             }
             int tot;
             const int ps = block_exscan1(cntc, tmp, spar, tot);
