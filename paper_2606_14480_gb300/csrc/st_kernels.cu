@@ -20,8 +20,15 @@
 //   k_match   one event per item: VELO segments bucketed by ty in shared
 //             memory, one thread per seed for its lowest chi2_match, then
 //             optionally the final selection (ghost network, clones).
+//
+// k_order, k_seed, k_scan and k_gather are launched as programmatic
+// dependents of the kernel before them in the stream: their CTAs may be
+// scheduled while it finishes, and wait (griddepcontrol.wait) for its
+// completion and its memory before they read or write anything it touches.
+// Launched without that attribute, the wait returns at once.
 #include <algorithm>
 #include <cfloat>
+#include <utility>
 
 #include "st_kernels.cuh"
 
@@ -31,6 +38,12 @@ typedef unsigned long long ull;
 
 
 static __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Programmatic dependent launch (PTX griddepcontrol): let the next kernel of
+// the stream be scheduled once every CTA of this grid has signalled or ended,
+// and wait for the completion and memory of the grids this one depends on.
+__device__ __forceinline__ void pdl_signal() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // First container index of event e: events are laid out back to back with
 // three spare entries each, rounded up to a multiple of four floats so that
@@ -120,6 +133,7 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
     }
     ull ctr[2] = {0, 0};
     int spar = 0;  // which half of tmp the next block scan uses
+    pdl_signal();  // k_order may be scheduled; it waits for this grid
     for (int k = tid; k < NB; k += T) cnt[k] = 0;
     if (tid == 0) {
         s_bad = 0;
@@ -281,6 +295,8 @@ constexpr int kOrderThreads = 1024;
 __global__ void __launch_bounds__(kOrderThreads) k_order(const __grid_constant__ BuildArgs A) {
     __shared__ int pos[kCostClasses], s_cnt[kCostClasses];
     const int tid = threadIdx.x;
+    pdl_signal();
+    pdl_wait();  // k_build's class counts
     const unsigned lane = tid & 31;
     if (tid < 32) {  // first place of each class: exclusive scan from the top class down
         constexpr int kPer = kCostClasses / 32;
@@ -464,6 +480,11 @@ __device__ int do_triplet(const DevParams& P, const IterP& I, const float* X, co
     o.score = nx == 6 ? sc : P.w5 * sc;
     return 2;
 }
+__device__ __noinline__ int do_triplet_out(const DevParams& P, const IterP& I, const float* X, const int* szl,
+                                          const uint16_t* lut, const float* sG, const int* sMask,
+                                          const uint32_t* used, int k1, int k2, int k3, Trip& o) {
+    return do_triplet(P, I, X, szl, lut, sG, sMask, used, k1, k2, k3, o);
+}
 
 // x(z) of a seed at stereo slot u (3-hit model plus fit correction)
 __device__ __forceinline__ float x_at_uv(const DevParams& P, const float* th, const float* dth, int u) {
@@ -524,7 +545,7 @@ __device__ void uv_chain(const DevParams& P, const float* X, const int* szl, con
 // in it, counted for all clusters at once with three bit planes.  The kept
 // clusters (most populated first, at least n_uv_min, ties to the smaller b)
 // go to out[]; returns how many.
-__device__ int hough_select(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
+__device__ __forceinline__ int hough_select_in(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
                             const uint32_t* used, const float* Xs, int h, uint8_t* out) {
     ull s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
@@ -560,10 +581,22 @@ __device__ int hough_select(const DevParams& P, const float* X, const int* szl, 
     return ns;
 }
 
+// The Hough functions, do_triplet and the cold paths of the UV step each
+// come as an inlined body (_in) and a call that is not inlined (_out).  The
+// seeding kernel calls the _out forms except in its HLT2-style
+// instantiation: their code and registers then stay out of the hot phases
+// of the iterative HLT1 path, which never runs the Hough code and rarely
+// the cold paths (measured 4.6% faster on the Run-3-like batch, while the
+// HLT2-style instantiation is faster with everything inlined).
+__device__ __noinline__ int hough_select_out(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
+                                             const uint32_t* used, const float* Xs, int h, uint8_t* out) {
+    return hough_select_in(P, X, szl, lut, used, Xs, h, out);
+}
+
 // step 2 for one t_y hypothesis: the closest hit within uv_tol in every
 // stereo layer (ties to the smaller x); stops once n_uv_min is out of reach.
-__device__ void uv_hough(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
-                         const uint32_t* used, const float* Xs, float ty, UV& o) {
+__device__ __forceinline__ void uv_hough_in(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
+                                           const uint32_t* used, const float* Xs, float ty, UV& o) {
     int n = 0;
     o.n = 0;
 #pragma unroll
@@ -580,6 +613,10 @@ __device__ void uv_hough(const DevParams& P, const float* X, const int* szl, con
     }
     o.n = n;
     o.tyr = ty;
+}
+__device__ __noinline__ void uv_hough_out(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
+                                          const uint32_t* used, const float* Xs, float ty, UV& o) {
+    uv_hough_in(P, X, szl, lut, used, Xs, ty, o);
 }
 
 __device__ __forceinline__ float hough_ty(const DevParams& P, int h, int b, int f) {
@@ -652,6 +689,58 @@ constexpr int kUvNotStored = 8191;
 __device__ __forceinline__ ull uv_key(int n, float chi2, int pass, int kinit, int stored) {
     return (ull(6 - n) << 61) | (ull(__float_as_uint(chi2) & 0x7fffffffu) << 30) | (ull(pass) << 29) |
            (ull(kinit) << 13) | ull(stored);
+}
+
+// x-z model of kept candidate k: th (3-hit model) and dth (fit correction),
+// stored as rows th0..2, dth0..2 of c_f
+struct XzModel {
+    float th[3], dth[3];
+};
+__device__ __forceinline__ XzModel xz_model(const float* c_f, int CC, int k) {
+    XzModel m;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        m.th[q] = c_f[q * CC + k];
+        m.dth[q] = c_f[(3 + q) * CC + k];
+    }
+    return m;
+}
+
+// Cold path of the UV step: a valid combination that found the chain store
+// full is fitted where it was found and takes part in the seed's choice by
+// its key alone (its hits are searched again if it wins).
+__device__ __forceinline__ void uv_fit_unstored_in(const DevParams& P, const float* X, const float* c_f, int CC,
+                                                   int k, UV u, ull* ukey, int pass, int kinit) {
+    const XzModel m = xz_model(c_f, CC, k);
+    uv_fit(P, X, m.th, m.dth, u);
+    atomicMin(ukey, uv_key(u.n, u.chi2, pass, kinit, kUvNotStored));
+}
+__device__ __noinline__ void uv_fit_unstored_out(const DevParams& P, const float* X, const float* c_f, int CC,
+                                                 int k, UV u, ull* ukey, int pass, int kinit) {
+    uv_fit_unstored_in(P, X, c_f, CC, k, u, ukey, pass, kinit);
+}
+
+// Cold path of the output step: the winning combination of a seed whose
+// hits were not stored, searched again (same chain, same result) and fitted.
+__device__ __forceinline__ UV uv_redo_in(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
+                                         const uint32_t* used, const float* Xs, const float* c_f, int CC, int k,
+                                         int h, const uint8_t* hc, ull key) {
+    const int kinit = static_cast<int>((key >> 13) & 0xFFFFu);
+    UV u;
+    if (P.uv_mode == 1) {
+        const int r = kinit / P.h_fine;
+        uv_hough_in(P, X, szl, lut, used, Xs, hough_ty(P, h, hc[r], kinit - r * P.h_fine), u);
+    } else {
+        uv_chain(P, X, szl, lut, used, Xs, static_cast<int>((key >> 29) & 1), kinit, u);
+    }
+    const XzModel m = xz_model(c_f, CC, k);
+    uv_fit(P, X, m.th, m.dth, u);
+    return u;
+}
+__device__ __noinline__ UV uv_redo_out(const DevParams& P, const float* X, const int* szl, const uint16_t* lut,
+                                       const uint32_t* used, const float* Xs, const float* c_f, int CC, int k, int h,
+                                       const uint8_t* hc, ull key) {
+    return uv_redo_in(P, X, szl, lut, used, Xs, c_f, CC, k, h, hc, key);
 }
 
 __device__ __forceinline__ ull pack_trip(int it, int k1, int k3, int k2) {
@@ -800,6 +889,7 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     // HLT2-style mode: bits of the half's hits taken by earlier iterations
     uint32_t* g_used = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(hn + CC) + 3) & ~uintptr_t(3));
     constexpr bool seq = kSeq;
+    constexpr bool kOut = !kSeq;  // the out-of-line forms of the rarely run functions
     const uint32_t* used = kSeq ? g_used : nullptr;
     __shared__ int s_nvalid, s_cnt, s_match;
     __shared__ ull s_mctr[4];  // grid pairs, preselected pairs, Long tracks, evaluated pairs
@@ -810,6 +900,8 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     // hits, valid UV chains, seeds): block totals, added up by thread 0
     __shared__ ull s_ctr[8];
     if (tid < 8) s_ctr[tid] = 0;
+    pdl_signal();
+    pdl_wait();  // the containers and the item order
 
     int64_t fin = -1;  // fused: event of the half this CTA finished last
     for (;;) {
@@ -1079,8 +1171,12 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                 if (t < ntrip) {
                     const ull tk = trip[t];
                     const int it = static_cast<int>(tk >> 60);
-                    code = do_triplet(P, P.it[it], X, szl, lut, sG, sMask, used, static_cast<int>((tk >> 40) & 0xFFFFF),
-                                      static_cast<int>(tk & 0xFFFFF), static_cast<int>((tk >> 20) & 0xFFFFF), o);
+                    const int k1 = static_cast<int>((tk >> 40) & 0xFFFFF), k2 = static_cast<int>(tk & 0xFFFFF);
+                    const int k3 = static_cast<int>((tk >> 20) & 0xFFFFF);
+                    if constexpr (kOut)
+                        code = do_triplet_out(P, P.it[it], X, szl, lut, sG, sMask, used, k1, k2, k3, o);
+                    else
+                        code = do_triplet(P, P.it[it], X, szl, lut, sG, sMask, used, k1, k2, k3, o);
                 }
                 // candidates in the low 16 bits, extended triplets (code >= 1)
                 // in the high ones: at most one each per thread, so no carry
@@ -1165,7 +1261,10 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
         __syncthreads();
         if (hough) {
             for (int j = kb + tid; j < nk; j += T)
-                hn[j] = static_cast<uint8_t>(hough_select(P, X, szl, lut, used, Xs + 6 * j, h, hcl + 8 * j));
+                if constexpr (kOut)
+                    hn[j] = static_cast<uint8_t>(hough_select_out(P, X, szl, lut, used, Xs + 6 * j, h, hcl + 8 * j));
+                else
+                    hn[j] = static_cast<uint8_t>(hough_select_in(P, X, szl, lut, used, Xs + 6 * j, h, hcl + 8 * j));
             __syncthreads();
         }
         // iterative: one item per (seed, pass), numbered pass-major (all pass
@@ -1216,8 +1315,11 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     UV u;
                     if (hough) {
                         const int r = kinit / P.h_fine;
-                        uv_hough(P, X, szl, lut, used, Xs + 6 * j, hough_ty(P, h, hcl[8 * j + r], kinit - r * P.h_fine),
-                                 u);
+                        const float ty = hough_ty(P, h, hcl[8 * j + r], kinit - r * P.h_fine);
+                        if constexpr (kOut)
+                            uv_hough_out(P, X, szl, lut, used, Xs + 6 * j, ty, u);
+                        else
+                            uv_hough_in(P, X, szl, lut, used, Xs + 6 * j, ty, u);
                     } else if (is_used(used, szl[6 + P.uv_init[pass]] + kinit)) {
                         u.n = 0;  // initial hit taken by an earlier iteration
                     } else {
@@ -1235,11 +1337,10 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                             vmeta[sidx] = make_uint2(unsigned(j), unsigned(pass) | (unsigned(kinit) << 1));
                         } else {
                             // store full: fit here; the winner is searched again at output
-                            const int k = kept[j];
-                            const float th[3] = {c_f[k], c_f[CC + k], c_f[2 * CC + k]};
-                            const float dth[3] = {c_f[3 * CC + k], c_f[4 * CC + k], c_f[5 * CC + k]};
-                            uv_fit(P, X, th, dth, u);
-                            atomicMin(&ukey[j], uv_key(u.n, u.chi2, pass, kinit, kUvNotStored));
+                            if constexpr (kOut)
+                                uv_fit_unstored_out(P, X, c_f, CC, kept[j], u, &ukey[j], pass, kinit);
+                            else
+                                uv_fit_unstored_in(P, X, c_f, CC, kept[j], u, &ukey[j], pass, kinit);
                         }
                     }
                     ++kinit;
@@ -1366,15 +1467,10 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
                     u.wm = f.z;
                     u.zm = f.w;
                 } else {
-                    const int kinit = static_cast<int>((key >> 13) & 0xFFFFu);
-                    if (P.uv_mode == 1) {
-                        const int r = kinit / P.h_fine;
-                        uv_hough(P, X, szl, lut, used, Xs + 6 * j, hough_ty(P, h, hcl[8 * j + r], kinit - r * P.h_fine),
-                                 u);
-                    } else {
-                        uv_chain(P, X, szl, lut, used, Xs + 6 * j, static_cast<int>((key >> 29) & 1), kinit, u);
-                    }
-                    uv_fit(P, X, th, dth, u);
+                    if constexpr (kOut)
+                        u = uv_redo_out(P, X, szl, lut, used, Xs + 6 * j, c_f, CC, k, h, hcl + 8 * j, key);
+                    else
+                        u = uv_redo_in(P, X, szl, lut, used, Xs + 6 * j, c_f, CC, k, h, hcl + 8 * j, key);
                 }
                 // the record goes out as 16-byte stores (pool rows are 48 /
                 // 32 / 16 bytes long and the pool is 256-byte aligned)
@@ -1419,6 +1515,8 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
 
 __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ GatherArgs A) {
     __shared__ int tmp[36];
+    pdl_signal();
+    pdl_wait();  // the seeding kernel's item counts
     int64_t carry = 0;
     for (int64_t b = 0; b < A.n_events; b += blockDim.x) {
         const int64_t e = b + threadIdx.x;
@@ -1438,6 +1536,7 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ GatherArg
 // (at most 32 registers: eight CTAs per SM, a 1000-event batch in one round)
 template <bool kVec>
 __global__ void __launch_bounds__(256, 8) k_gather(const __grid_constant__ GatherArgs A) {
+    pdl_wait();  // the event offsets (and, through k_scan, the seed records)
     const bool fault = A.fault && *A.fault;
     for (int64_t e = blockIdx.x; e < A.n_events; e += gridDim.x) {
         if (fault && threadIdx.x == 0) A.status[e] = -4;  // ST_TIMEOUT: the fused matching gave up a wait
@@ -1925,46 +2024,59 @@ int match_blocks_per_sm(int threads, size_t smem) {
     return n;
 }
 
+// A launch as a programmatic dependent of the stream's previous kernel
+// (chained), or a plain one.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*k)(KArgs...), unsigned grid, unsigned threads, size_t smem, cudaStream_t s,
+                            bool chained, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = chained ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int threads, cudaStream_t s) {
     k_build<<<grid, threads, build_smem_bytes(a.bins, a.smem_hits), s>>>(P, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t items = 2 * a.n_events;
     if (items <= 0) return cudaSuccess;
-    k_order<<<static_cast<unsigned>((items + kOrderThreads - 1) / kOrderThreads), kOrderThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_k(k_order, static_cast<unsigned>((items + kOrderThreads - 1) / kOrderThreads), kOrderThreads, 0, s,
+                    true, a);
 }
 
-cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s) {
+cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s, bool chained) {
     const size_t smem = seed_smem_bytes(threads, a.smem_hits, a.tbl_smem, a.key_smem);
     const bool sq = P.iter_mode == 1;
+    void (*k)(const DevParams, const SeedArgs);
     if (a.velo) {  // fused matching: the runtime only asks for it where this instantiation applies
         if (threads > 256 || sq) return cudaErrorInvalidValue;
-        k_seed<256, kSeedBlocks256, false, true><<<grid, threads, smem, s>>>(P, a);
+        k = k_seed<256, kSeedBlocks256, false, true>;
     } else if (threads <= 256) {
-        if (sq) k_seed<256, kSeedBlocks256, true, false><<<grid, threads, smem, s>>>(P, a);
-        else k_seed<256, kSeedBlocks256, false, false><<<grid, threads, smem, s>>>(P, a);
+        k = sq ? k_seed<256, kSeedBlocks256, true, false> : k_seed<256, kSeedBlocks256, false, false>;
     } else {
-        if (sq) k_seed<kMaxThreads, 2, true, false><<<grid, threads, smem, s>>>(P, a);
-        else k_seed<kMaxThreads, 2, false, false><<<grid, threads, smem, s>>>(P, a);
+        k = sq ? k_seed<kMaxThreads, 2, true, false> : k_seed<kMaxThreads, 2, false, false>;
     }
-    return cudaGetLastError();
+    return launch_k(k, static_cast<unsigned>(grid), static_cast<unsigned>(threads), smem, s, chained, P, a);
 }
 
-cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s) {
-    k_scan<<<1, 1024, 0, s>>>(a);
-    cudaError_t err = cudaGetLastError();
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s, bool chained) {
+    cudaError_t err = launch_k(k_scan, 1, 1024, 0, s, chained, a);
     if (err != cudaSuccess) return err;
     const int grid = static_cast<int>(std::min<int64_t>(a.n_events, 8192));
     if (grid <= 0) return cudaSuccess;
     // pool arrays are 256-byte aligned; the caller's output arrays may not be
     const uintptr_t mis = (reinterpret_cast<uintptr_t>(a.hits) | reinterpret_cast<uintptr_t>(a.params) |
                            reinterpret_cast<uintptr_t>(a.state)) & 15u;
-    if (mis == 0 && (reinterpret_cast<uintptr_t>(a.n_hits) & 1u) == 0)
-        k_gather<true><<<grid, 256, 0, s>>>(a);
-    else
-        k_gather<false><<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    const bool vec = mis == 0 && (reinterpret_cast<uintptr_t>(a.n_hits) & 1u) == 0;
+    return launch_k(vec ? k_gather<true> : k_gather<false>, static_cast<unsigned>(grid), 256, 0, s, true, a);
 }
 
 cudaError_t launch_match(const DevParams& P, const MatchArgs& a, int grid, int threads, cudaStream_t s) {

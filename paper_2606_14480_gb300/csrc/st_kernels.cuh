@@ -130,8 +130,11 @@ size_t seed_slot_bytes(int cand_cap, int max_xhits);
 size_t match_smem_bytes(int velo_smem);
 
 cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int threads, cudaStream_t s);
-cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s);
-cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
+// chained: launched as a programmatic dependent of the stream's previous
+// kernel (the caller puts no other stream work between the two)
+cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s,
+                        bool chained = true);
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s, bool chained = true);
 cudaError_t launch_match(const DevParams& P, const MatchArgs& a, int grid, int threads, cudaStream_t s);
 
 // occupancy helpers

@@ -761,8 +761,11 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
         a.n_long = L->n_long;
         if (ctx->timing && &w == &ctx->ws) ctx->tused[3] = false;  // matching runs inside k_seed
     }
+    // the seeding kernel and the scan follow their predecessors as
+    // programmatic dependents, except where timing marks come between
+    const bool marks = ctx->timing && &w == &ctx->ws;
     tmark(ctx, w, 1, 0, s);
-    ST_CUDA(ctx, launch_seed(ctx->P, a, g_seed, c.threads_seed, s));
+    ST_CUDA(ctx, launch_seed(ctx->P, a, g_seed, c.threads_seed, s, !marks));
     tmark(ctx, w, 1, 1, s);
 
     GatherArgs g;
@@ -788,7 +791,7 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
         g.fault = w.queues + 4;
     }
     tmark(ctx, w, 2, 0, s);
-    ST_CUDA(ctx, launch_gather(g, s));
+    ST_CUDA(ctx, launch_gather(g, s, !marks));
     tmark(ctx, w, 2, 1, s);
     return ST_OK;
 }
