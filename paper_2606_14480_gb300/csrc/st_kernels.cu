@@ -2042,14 +2042,14 @@ static cudaError_t launch_k(void (*k)(KArgs...), unsigned grid, unsigned threads
     return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
-cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int threads, cudaStream_t s) {
+cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int threads, cudaStream_t s, bool chained) {
     k_build<<<grid, threads, build_smem_bytes(a.bins, a.smem_hits), s>>>(P, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t items = 2 * a.n_events;
     if (items <= 0) return cudaSuccess;
     return launch_k(k_order, static_cast<unsigned>((items + kOrderThreads - 1) / kOrderThreads), kOrderThreads, 0, s,
-                    true, a);
+                    chained, a);
 }
 
 cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s, bool chained) {

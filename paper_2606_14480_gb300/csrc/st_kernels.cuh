@@ -129,9 +129,13 @@ size_t seed_smem_bytes(int threads, int smem_hits, int tbl_smem, int key_smem);
 size_t seed_slot_bytes(int cand_cap, int max_xhits);
 size_t match_smem_bytes(int velo_smem);
 
-cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int threads, cudaStream_t s);
-// chained: launched as a programmatic dependent of the stream's previous
-// kernel (the caller puts no other stream work between the two)
+// chained: k_order, k_seed and k_scan are launched as programmatic dependents
+// of the stream's previous kernel (the caller puts no other stream work
+// between them; k_gather always follows k_scan that way).  Their CTAs may
+// then wait on the SMs for that kernel, which only pays where no other
+// stream's kernels want those SMs.
+cudaError_t launch_build(const DevParams& P, const BuildArgs& a, int grid, int threads, cudaStream_t s,
+                         bool chained = true);
 cudaError_t launch_seed(const DevParams& P, const SeedArgs& a, int grid, int threads, cudaStream_t s,
                         bool chained = true);
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s, bool chained = true);

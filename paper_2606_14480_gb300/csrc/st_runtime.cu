@@ -715,8 +715,16 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
     b.zero2 = fused ? w.ev_done : nullptr;  // halves done + announcements, cleared before k_seed
     b.queue = w.queues + 0;
     b.counters = ctx->counters;
+    // k_order, the seeding kernel and the scan follow their predecessors as
+    // programmatic dependents on the context's own workspace, except where
+    // timing marks come between.  Not on the serving pipeline's slot
+    // streams: CTAs waiting there for their predecessor hold SMs that the
+    // other slots' kernels could use (measured: 24% less served throughput
+    // at saturation).
+    const bool marks = ctx->timing && &w == &ctx->ws;
+    const bool chain = &w == &ctx->ws;
     tmark(ctx, w, 0, 0, s);
-    ST_CUDA(ctx, launch_build(ctx->P, b, g_build, c.threads_build, s));
+    ST_CUDA(ctx, launch_build(ctx->P, b, g_build, c.threads_build, s, chain));
     tmark(ctx, w, 0, 1, s);
 
     SeedArgs a;
@@ -761,11 +769,8 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
         a.n_long = L->n_long;
         if (ctx->timing && &w == &ctx->ws) ctx->tused[3] = false;  // matching runs inside k_seed
     }
-    // the seeding kernel and the scan follow their predecessors as
-    // programmatic dependents, except where timing marks come between
-    const bool marks = ctx->timing && &w == &ctx->ws;
     tmark(ctx, w, 1, 0, s);
-    ST_CUDA(ctx, launch_seed(ctx->P, a, g_seed, c.threads_seed, s, !marks));
+    ST_CUDA(ctx, launch_seed(ctx->P, a, g_seed, c.threads_seed, s, chain && !marks));
     tmark(ctx, w, 1, 1, s);
 
     GatherArgs g;
@@ -791,7 +796,7 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
         g.fault = w.queues + 4;
     }
     tmark(ctx, w, 2, 0, s);
-    ST_CUDA(ctx, launch_gather(g, s, !marks));
+    ST_CUDA(ctx, launch_gather(g, s, chain && !marks));
     tmark(ctx, w, 2, 1, s);
     return ST_OK;
 }
