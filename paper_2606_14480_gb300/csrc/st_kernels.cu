@@ -249,9 +249,12 @@ k_build(const __grid_constant__ DevParams P, const __grid_constant__ BuildArgs A
         for (int i = tid; i < n; i += T) pm[atomicAdd(&cnt[bk[i]], 1)] = static_cast<uint16_t>(i);
         __syncthreads();
         // rank of each hit in its bucket -> its place in the sorted event;
-        // the cursors are cleared for the next event
+        // the cursors are cleared for the next event.  Threads take the hits
+        // in bucket order, so the lanes of a warp mostly share a bucket: equal
+        // loop lengths, and the bucket's reads are broadcasts.
         for (int k = tid; k < NB; k += T) cnt[k] = 0;
-        for (int i = tid; i < n; i += T) {
+        for (int d = tid; d < n; d += T) {
+            const int i = pm[d];
             const int b = bk[i], s = off[b], c = off[b + 1] - s;
             const float x = hx[i];
             int r = 0;
