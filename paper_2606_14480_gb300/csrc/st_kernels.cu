@@ -45,6 +45,46 @@ static __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~
 __device__ __forceinline__ void pdl_signal() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Bulk copies (the TMA's untiled form, cp.async.bulk) into shared memory,
+// completing on an mbarrier: one thread initialises the barrier, one thread
+// issues each copy with the byte count it expects, every thread waits for the
+// phase.  Both addresses 16-byte aligned, the size a multiple of 16 bytes.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(ull* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigned bytes, ull* b) {
+    // the CTA's earlier reads of dst (ordered by a barrier) before the copy's writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(b))
+                 : "memory");
+}
+// Polls the barrier's phase `parity`; false after max_polls unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(ull* b, unsigned parity, int max_polls) {
+    const uint32_t a = smem_addr(b);
+    for (int i = 0; i < max_polls; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+// A staging copy that has not landed after this many polls (each of which
+// may suspend the thread for a while) is given up: the launch is marked
+// faulty and the item reads its hits from global memory.
+constexpr int kStagePolls = 1 << 22;
+
 // First container index of event e: events are laid out back to back with
 // three spare entries each, rounded up to a multiple of four floats so that
 // every event starts 16-byte aligned.
@@ -903,6 +943,11 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
     // hits, valid UV chains, seeds): block totals, added up by thread 0
     __shared__ ull s_ctr[8];
     if (tid < 8) s_ctr[tid] = 0;
+    // the staging copies' barrier (one phase per staged item)
+    __shared__ ull s_mbar;
+    if (tid == 0) mbar_init(&s_mbar, 1);
+    unsigned mphase = 0;
+    bool stage_ok = true;
     pdl_signal();
     pdl_wait();  // the containers and the item order
 
@@ -1010,18 +1055,24 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
         const int nh = zo[12] - zo[0];
         if (tid <= 12) szl[tid] = zo[tid] - zo[0];
         const float* X = A.cx + cbh;
-        if (nh <= A.smem_hits) {
-            // four loads per thread in flight
-            int i = tid;
-            for (; i + 3 * T < nh; i += 4 * T) {
-                const float a0 = X[i], a1 = X[i + T], a2 = X[i + 2 * T], a3 = X[i + 3 * T];
-                sx[i] = a0;
-                sx[i + T] = a1;
-                sx[i + 2 * T] = a2;
-                sx[i + 3 * T] = a3;
+        // the half's hits are one contiguous slice: staged in shared memory by
+        // one bulk copy of the 16-byte words that hold it (the container's
+        // events start 16-byte aligned and are padded to a multiple of 16 bytes)
+        const int64_t w0 = cbh & ~int64_t(3);
+        const int lead = static_cast<int>(cbh - w0);
+        const int nw = (lead + nh + 3) & ~3;
+        if (stage_ok && nh > 0 && nw <= A.smem_hits) {
+            if (tid == 0) bulk_to_smem(sx, A.cx + w0, 4u * unsigned(nw), &s_mbar);
+            const bool got = mbar_wait(&s_mbar, mphase, kStagePolls);
+            mphase ^= 1u;
+            if (__syncthreads_or(!got)) {
+                // the copy did not land: global reads from here on, the launch
+                // marked faulty (every event then gets ST_TIMEOUT)
+                stage_ok = false;
+                if (tid == 0 && A.fault) atomicExch(A.fault, 1);
+            } else {
+                X = sx + lead;
             }
-            for (; i < nh; i += T) sx[i] = X[i];
-            X = sx;
         }
         __syncthreads();
 
@@ -1507,6 +1558,9 @@ k_seed(const __grid_constant__ DevParams P, const __grid_constant__ SeedArgs A) 
         }
     }
     __syncthreads();
+    // a copy given up on may still land: wait for it (bounded) before the
+    // CTA's shared memory goes away
+    if (!stage_ok) mbar_wait(&s_mbar, mphase ^ 1u, kStagePolls);
     if (tid < 8 && s_ctr[tid]) atomicAdd(A.counters + C_PAIRS + tid, s_ctr[tid]);
     if (kFuse && tid < 3 && s_mctr[tid]) atomicAdd(A.counters + C_MATCH_PAIRS + tid, s_mctr[tid]);
     if (kFuse && tid == 3 && s_mctr[3]) atomicAdd(A.counters + C_MATCH_EVAL, s_mctr[3]);

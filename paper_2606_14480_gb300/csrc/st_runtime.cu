@@ -752,6 +752,7 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
     a.order = w.order;
     a.queue = w.queues + 1;
     a.counters = ctx->counters;
+    a.fault = w.queues + 4;  // a wait that gave up (staging copy, announced event)
     if (fused) {
         a.velo_off = V->ev_off;
         a.velo = V->state;
@@ -760,7 +761,6 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
         a.ev_done = w.ev_done;
         a.ready = w.ev_done + H.n_events;
         a.ready_ctr = w.queues + 3;
-        a.fault = w.queues + 4;
         a.wait_ns = static_cast<unsigned long long>(ctx->wait_ns);
         a.m_claim = w.queues + 5;
         a.done_ctr = w.queues + 6;
@@ -788,12 +788,12 @@ static int run_seeding(st_ctx* ctx, Workspace& w, const st_hits& H, st_seeds& S,
     g.state = S.state;
     g.n_hits = S.n_hits;
     g.status = S.status;
+    g.fault = w.queues + 4;
     if (fused) {
         g.pool_velo = w.pool_velo;
         g.pool_chi2 = w.pool_chi2;
         g.velo_idx = L->velo_idx;
         g.chi2 = L->chi2;
-        g.fault = w.queues + 4;
     }
     tmark(ctx, w, 2, 0, s);
     ST_CUDA(ctx, launch_gather(g, s, chain && !marks));

@@ -234,6 +234,7 @@ extern "C" int seeding_run_static(const st_config* cfg, const st_hits* H, st_see
     sa.order = ba.order;
     sa.queue = queues + 1;
     sa.counters = counters;
+    sa.fault = queues + 4;  // set if a staging copy was given up on
     e = launch_seed(P, sa, g_seed, cfg->threads_seed, s);
     if (e != cudaSuccess) return fail(err, err_len, ST_ECUDA, "k_seed: %s", cudaGetErrorString(e));
 
@@ -252,6 +253,7 @@ extern "C" int seeding_run_static(const st_config* cfg, const st_hits* H, st_see
     ga.state = S->state;
     ga.n_hits = S->n_hits;
     ga.status = S->status;
+    ga.fault = sa.fault;
     e = launch_gather(ga, s);
     if (e != cudaSuccess) return fail(err, err_len, ST_ECUDA, "gather: %s", cudaGetErrorString(e));
     return ST_OK;
