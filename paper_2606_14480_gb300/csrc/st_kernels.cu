@@ -393,10 +393,13 @@ __global__ void __launch_bounds__(kOrderThreads) k_order(const __grid_constant__
 // The range covers the SciFi's x acceptance (|x| < 3200 mm) and the stereo
 // layers' measured coordinate, offset from it by y tan(5 deg) for |y| < 2500 mm
 // (hits outside it fall into the end buckets, which stays correct but scans
-// longer).  Finer buckets than the 32 mm of a [-4096, 4096) range shorten the
-// scans (k_seed 0.2088 -> 0.206 ms for 1000 Run-3-like events).
+// longer).  Finer buckets shorten the scans: against 32 mm buckets over
+// [-4096, 4096), 27 mm took k_seed from 0.2088 to 0.206 ms for 1000
+// Run-3-like events; 18 mm keeps that step time and takes 12% off the
+// 10 000-event uneven batch, whose large events hold more hits per bucket
+// (9 KB of tables per CTA).
 constexpr float kLutRange = 3456.f;
-constexpr int kLutBins = 256;  // 27 mm buckets over [-3456, 3456) mm
+constexpr int kLutBins = 384;  // 18 mm buckets over [-3456, 3456) mm
 
 __device__ __forceinline__ int lut_bin(float v) {
     const int b = __float2int_rd((v + kLutRange) * (kLutBins / (2.f * kLutRange)));
