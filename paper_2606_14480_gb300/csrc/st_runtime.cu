@@ -610,7 +610,7 @@ extern "C" int st_create(const st_config* cfg, int device, st_ctx** out) {
     ctx->smem_optin = optin;
     const st_config& c = *cfg;
     ctx->tbl_smem = c.smem_hits / 2;
-    ctx->key_smem = std::max(64, c.smem_hits / 6);  // kept seeds whose UV keys and stereo x stay in shared memory
+    ctx->key_smem = std::max(64, c.smem_hits / 8);  // kept seeds whose UV keys and stereo x stay in shared memory
     ctx->velo_smem = 512;
     ctx->seed_smem = seed_smem_bytes(c.threads_seed, c.smem_hits, ctx->tbl_smem, ctx->key_smem);
     ctx->match_smem = match_smem_bytes(ctx->velo_smem);

@@ -166,7 +166,7 @@ extern "C" int seeding_run_static(const st_config* cfg, const st_hits* H, st_see
     int bins = 8;
     while (bins < 512 && bins * 96 < mh) bins <<= 1;
     const size_t bsmem = build_smem_bytes(bins, static_cast<int>(mh));
-    const int tbl_smem = cfg->smem_hits / 2, key_smem = std::max(64, cfg->smem_hits / 6);  // as st_create
+    const int tbl_smem = cfg->smem_hits / 2, key_smem = std::max(64, cfg->smem_hits / 8);  // as st_create
     const size_t ssmem = seed_smem_bytes(cfg->threads_seed, cfg->smem_hits, tbl_smem, key_smem);
     // the shared-memory check of st_create (2 KB left for static shared memory)
     if (ssmem + 2048 > size_t(D->optin) || bsmem + 2048 > size_t(D->optin))
