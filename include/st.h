@@ -37,7 +37,7 @@ typedef enum {
     ST_EINVAL = -1,     /* invalid argument / input */
     ST_ENOMEM = -2,     /* device or pinned allocation failed */
     ST_OVERFLOW = -3,   /* a capacity was exceeded (per event, or call-level) */
-    ST_TIMEOUT = -4,    /* pipeline_poll: the wait ran out */
+    ST_TIMEOUT = -4,    /* pipeline_poll: the wait ran out; per event: a bounded device wait gave up */
     ST_ECUDA = -5,      /* a CUDA runtime call failed; see st_last_error */
     ST_ESTATE = -6      /* call not valid in the context's current state */
 } st_status;
@@ -238,6 +238,10 @@ int st_reserve(st_ctx* ctx, int64_t n_events, int64_t n_hits, int32_t max_hits_p
  * Output `seeds` as described at st_seeds.  Returns ST_EINVAL for a bad
  * argument (NULL array, cap < 0, n_events < 0), ST_ENOMEM / ST_ECUDA for
  * allocation or launch failures; per-event problems go to seeds->status.
+ * Each (event, half) work item's hits are staged in shared memory by one
+ * bulk copy whose completion the kernel waits for with a bound; a copy that
+ * never lands (which a working device cannot produce) gives every event of
+ * the launch ST_TIMEOUT.
  * Allocates scratch if st_reserve was not called for this size. */
 int seeding_run(st_ctx* ctx, const st_hits* hits, st_seeds* seeds, void* cuda_stream);
 
