@@ -827,7 +827,7 @@ __device__ __forceinline__ int pair_window(const DevParams& P, const IterP& I, c
 }
 
 constexpr int kTripPerCand = 2;  // triplet buffer entries per candidate slot
-constexpr int kTripLocal = 8;    // triplets a thread buffers while walking its pairs
+constexpr int kTripLocal = 12;   // triplets a thread buffers while walking its pairs
 
 size_t seed_smem_bytes(int threads, int smem_hits, int tbl_smem, int key_smem) {
     return align16(sizeof(float) * smem_hits) + align16(sizeof(uint16_t) * 12 * kLutBins) +

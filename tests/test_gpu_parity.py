@@ -149,6 +149,25 @@ def test_deterministic_across_launch_shapes(zmx):
             assert np.array_equal(ref[k], gpu[k]), (tune, k)
 
 
+def test_staging_boundary(zmx):
+    """A half is staged in shared memory by one bulk copy of the 16-byte words
+    that hold it (up to three floats more on each side) when those fit the
+    staging budget, else read from global memory.  Budgets around one half's
+    size (below it, at it, and up to seven hits above it) flip that choice for
+    it and for halves of nearby sizes; every result equals the default
+    budget's, which equals the oracle's (test_seeding_parity)."""
+    b = workload("run3", n_events=40)
+    half1 = np.array([int(np.count_nonzero(b.hits_of(e)[1] & 1)) for e in range(b.n_events)])
+    n = int(np.median(half1))
+    _, gcfg = parity.config_pair(zmx)
+    ref, _ = run_gpu(b, gcfg)
+    for s in (n - 1, n, n + 1, n + 3, n + 6, n + 7):
+        _, gcfg = parity.config_pair(zmx, smem_hits=s)
+        gpu, _ = run_gpu(b, gcfg)
+        for k in ref:
+            assert np.array_equal(ref[k], gpu[k]), (s, k)
+
+
 def test_graph_replay_matches_direct_run(zmx):
     b = workload("run3", n_events=100)
     _, gcfg = parity.config_pair(zmx)
