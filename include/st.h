@@ -368,7 +368,7 @@ int st_read_counters(st_ctx* ctx, st_counters* out, int reset);
  * current for the calling thread.  The results equal seeding_run's.
  * Limits: max_hits_per_event <= 6144, and the batch must fit the array:
  * (8*max_hits_per_event + 156) bytes per event plus 98*seeds->cap bytes plus
- * one candidate store of about 112*cand_cap + 8*max_hits_per_event + 360 KB
+ * one candidate store of about 121*cand_cap + 8*max_hits_per_event + 377 KB
  * (e.g. 128 events of up to 4096 hits with 40 000 seeds fit); otherwise it
  * returns ST_OVERFLOW, writes nothing, and the message gives the exact byte
  * count the batch needs.  A configuration whose shared-memory needs exceed
